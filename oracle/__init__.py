@@ -1,0 +1,216 @@
+"""ctypes front end of the sequential CPU oracle (``oracle/nk_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and the cpu_baseline /
+reference leg of ``bench.py`` are the only callers.  The product library never imports
+this package, and this package never imports the product library.
+
+Every function mirrors one C function and cites the passage of the paper it follows:
+Brandes' algorithm and the sampled estimate (Section 3.2, Table 1), BFS for unweighted
+graphs (Section 3.4), the generators of Section 5 (Table 2).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "nk_oracle.c")
+_OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_ARG, ERR_GRAPH, ERR_NOMEM, ERR_OVERFLOW = 0, -1, -2, -3, -4
+
+
+class OracleError(RuntimeError):
+    def __init__(self, rc: int, what: str):
+        super().__init__(f"oracle {what} failed with code {rc}")
+        self.rc = rc
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (contraction off: the ER skip arithmetic is then the
+    same sequence of IEEE operations on x86 and Arm hosts)."""
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+        tmp = _OUT + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        i32, i64, u64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+        P = ctypes.c_void_p
+        sig = {
+            "or_mix64": (u64, [u64]),
+            "or_stream": (u64, [u64, u64]),
+            "or_log": (dbl, [dbl]),
+            "or_gen_er": (i64, [i32, dbl, u64, P, P, i64]),
+            "or_gen_ba": (i64, [i32, i32, u64, P, P, i64]),
+            "or_gen_rmat": (i64, [i32, i32, dbl, dbl, dbl, u64, P, P, i64]),
+            "or_csr_build": (i64, [i32, i64, P, P, P, P]),
+            "or_sample_sources": (ctypes.c_int, [i32, u64, i32, P]),
+            "or_bfs": (ctypes.c_int, [i32, P, P, i32, P, P]),
+            "or_dependencies": (ctypes.c_int, [i32, P, P, i32, P]),
+            "or_betweenness": (ctypes.c_int, [i32, P, P, i32, P, dbl, P]),
+            "or_betweenness_exact": (ctypes.c_int, [i32, P, P, P]),
+            "or_betweenness_sampled": (ctypes.c_int, [i32, P, P, u64, i32, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype, f.argtypes = res, args
+        _lib = lib
+        return lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+# ---------------------------------------------------------------- random numbers
+def mix64(z: int) -> int:
+    return int(_load().or_mix64(z))
+
+
+def stream(seed: int, i: int) -> int:
+    """i-th output of SplitMix64 seeded with ``seed`` (Steele, Lea, Flood 2014)."""
+    return int(_load().or_stream(seed, i))
+
+
+def log(x: float) -> float:
+    """The ER generator's logarithm (atanh series), for 0 < x <= 1."""
+    return float(_load().or_log(x))
+
+
+# ---------------------------------------------------------------- generators (Section 5)
+def _two_pass(fn, *args):
+    m = fn(*args, None, None, 0)
+    if m < 0:
+        raise OracleError(m, fn.__name__)
+    eu = np.empty(max(m, 1), np.int32)
+    ev = np.empty(max(m, 1), np.int32)
+    m2 = fn(*args, _p(eu), _p(ev), m)
+    assert m2 == m
+    return eu[:m], ev[:m]
+
+
+def gen_er(n: int, avg_deg: float, seed: int):
+    """Erdos-Renyi G(n, p = avg_deg/(n-1)) by chunked geometric skipping."""
+    return _two_pass(_load().or_gen_er, n, avg_deg, seed)
+
+
+def gen_ba(n: int, m0: int, seed: int):
+    """Barabasi-Albert linear preferential attachment, m0 edges per new vertex."""
+    return _two_pass(_load().or_gen_ba, n, m0, seed)
+
+
+def gen_rmat(scale: int, edge_factor: int, a: float, b: float, c: float, seed: int):
+    """R-MAT with 2^scale vertices and edge_factor * 2^scale raw edges."""
+    return _two_pass(_load().or_gen_rmat, scale, edge_factor, a, b, c, seed)
+
+
+def csr_build(n: int, eu, ev):
+    """Canonical CSR (symmetrised, no self-loops, sorted, no duplicates)."""
+    eu, ev = _i32(eu), _i32(ev)
+    m = len(eu)
+    rp = np.empty(n + 1, np.int32)
+    col = np.empty(max(2 * m, 1), np.int32)
+    A = _load().or_csr_build(n, m, _p(eu), _p(ev), _p(rp), _p(col))
+    if A < 0:
+        raise OracleError(A, "csr_build")
+    return rp, col[:A].copy()
+
+
+def generate(kind: str, size: int, seed: int, **params):
+    """Raw edges of one of the three generators, then the canonical CSR: (n, rp, col)."""
+    if kind == "er":
+        eu, ev = gen_er(size, params.get("avg_deg", 8.0), seed)
+        n = size
+    elif kind == "ba":
+        eu, ev = gen_ba(size, int(params.get("m0", 8)), seed)
+        n = size
+    elif kind == "rmat":
+        eu, ev = gen_rmat(size, int(params.get("edge_factor", 16)), params.get("a", 0.57),
+                          params.get("b", 0.19), params.get("c", 0.19), seed)
+        n = 1 << size
+    else:
+        raise ValueError(kind)
+    rp, col = csr_build(n, eu, ev)
+    return n, rp, col
+
+
+# ---------------------------------------------------------------- sampler (Section 3.2)
+def sample_sources(n: int, seed: int, k: int) -> np.ndarray:
+    src = np.empty(k, np.int32)
+    rc = _load().or_sample_sources(n, seed, k, _p(src))
+    if rc:
+        raise OracleError(rc, "sample_sources")
+    return src
+
+
+# ---------------------------------------------------------------- BFS / Brandes
+def bfs(rp, col, s: int):
+    """(dist int32[n], sigma uint64[n]) from source s; raises on sigma overflow."""
+    rp, col = _i32(rp), _i32(col)
+    n = len(rp) - 1
+    dist = np.empty(n, np.int32)
+    sigma = np.empty(n, np.uint64)
+    rc = _load().or_bfs(n, _p(rp), _p(col), s, _p(dist), _p(sigma))
+    if rc:
+        raise OracleError(rc, "bfs")
+    return dist, sigma
+
+
+def dependencies(rp, col, s: int) -> np.ndarray:
+    rp, col = _i32(rp), _i32(col)
+    n = len(rp) - 1
+    delta = np.empty(n, np.float64)
+    rc = _load().or_dependencies(n, _p(rp), _p(col), s, _p(delta))
+    if rc:
+        raise OracleError(rc, "dependencies")
+    return delta
+
+
+def betweenness_sources(rp, col, src, scale: float) -> np.ndarray:
+    rp, col, src = _i32(rp), _i32(col), _i32(src)
+    n = len(rp) - 1
+    out = np.empty(n, np.float64)
+    rc = _load().or_betweenness(n, _p(rp), _p(col), len(src), _p(src), scale, _p(out))
+    if rc:
+        raise OracleError(rc, "betweenness")
+    return out
+
+
+def betweenness_exact(rp, col) -> np.ndarray:
+    rp, col = _i32(rp), _i32(col)
+    n = len(rp) - 1
+    out = np.empty(n, np.float64)
+    rc = _load().or_betweenness_exact(n, _p(rp), _p(col), _p(out))
+    if rc:
+        raise OracleError(rc, "betweenness_exact")
+    return out
+
+
+def betweenness_sampled(rp, col, seed: int, k: int) -> np.ndarray:
+    rp, col = _i32(rp), _i32(col)
+    n = len(rp) - 1
+    out = np.empty(n, np.float64)
+    rc = _load().or_betweenness_sampled(n, _p(rp), _p(col), seed, k, _p(out))
+    if rc:
+        raise OracleError(rc, "betweenness_sampled")
+    return out

@@ -1,0 +1,458 @@
+"""Pins for the CPU oracle: closed forms, brute force, invariants and published values.
+
+These tests check the oracle against things other than itself (the paper's definition
+of betweenness written as closed forms, an independent brute-force enumeration,
+mathematical invariants, published generator outputs), so that a dropped term, a wrong
+sign or index, or a transposed operand in the oracle fails at least one of them.
+"""
+from __future__ import annotations
+
+import math
+import os
+from fractions import Fraction
+from math import comb, factorial
+
+import numpy as np
+import pytest
+
+import graphs as G
+import oracle
+from bruteforce import betweenness_bruteforce, floyd_warshall, sssp_bruteforce
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def csr(graph):
+    n, u, v = graph
+    rp, col = oracle.csr_build(n, u, v)
+    return n, rp, col
+
+
+def exact(graph):
+    n, rp, col = csr(graph)
+    return oracle.betweenness_exact(rp, col)
+
+
+def read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append([int(x) for x in line.split()])
+    return rows
+
+
+# ------------------------------------------------------------------ random numbers
+def test_splitmix64_published_vectors():
+    want = [r[0] for r in read_golden("splitmix64_seed1234567.txt")]
+    got = [oracle.stream(1234567, i) for i in range(5)]
+    assert got == want
+
+
+def test_log_series_matches_libm():
+    xs = np.concatenate([np.linspace(2.0 ** -53, 1.0, 4001),
+                         1.0 - np.arange(1, 2000) * 2.0 ** -53,
+                         2.0 ** -np.arange(0, 53, dtype=np.float64)])
+    for x in xs:
+        got, want = oracle.log(float(x)), math.log(float(x))
+        assert abs(got - want) <= 4 * np.spacing(abs(want)) + 1e-300, (x, got, want)
+    assert oracle.log(1.0) == 0.0
+
+
+# ------------------------------------------------------------------ CSR builder
+def test_csr_canonical_form():
+    g = G.gnp(40, 0.2, 7)
+    n, rp, col = csr(g)
+    _, rp2, col2 = csr(G.noisy(g, 3))
+    assert np.array_equal(rp, rp2) and np.array_equal(col, col2)
+    adj = set()
+    for x in range(n):
+        row = col[rp[x]:rp[x + 1]]
+        assert np.all(np.diff(row) > 0)          # sorted, no duplicates
+        assert x not in row                      # no self-loops
+        adj.update((x, int(y)) for y in row)
+    assert all((y, x) in adj for x, y in adj)  # symmetric
+    assert len(adj) == 2 * len({(min(a, b), max(a, b)) for a, b in zip(g[1], g[2])})
+
+
+def test_csr_rejects_out_of_range():
+    with pytest.raises(oracle.OracleError):
+        oracle.csr_build(3, np.array([0, 3], np.int32), np.array([1, 0], np.int32))
+
+
+# ------------------------------------------------------------------ distances
+@pytest.mark.parametrize("graph", [G.path(9), G.cycle(10), G.cycle(11), G.grid(4, 6),
+                                   G.gnp(30, 0.1, 1), G.gnp(64, 0.05, 2),
+                                   G.disjoint_union(G.path(5), G.star(6), G.complete(4))])
+def test_bfs_distances_match_floyd_warshall(graph):
+    n, rp, col = csr(graph)
+    d = floyd_warshall(*graph)
+    for s in range(n):
+        dist, _ = oracle.bfs(rp, col, s)
+        assert np.array_equal(dist, d[s])
+
+
+def test_distance_closed_forms():
+    n, rp, col = csr(G.cycle(13))
+    for s in (0, 5):
+        dist, sigma = oracle.bfs(rp, col, s)
+        j = np.arange(n)
+        assert np.array_equal(dist, np.minimum(np.abs(j - s), n - np.abs(j - s)))
+        assert np.all(sigma == 1)  # odd cycle: unique shortest paths
+    n, rp, col = csr(G.cycle(12))
+    dist, sigma = oracle.bfs(rp, col, 0)
+    assert sigma[6] == 2 and np.all(np.delete(sigma, 6) == 1)
+
+
+# ------------------------------------------------------------------ path counts
+def test_sigma_grid_binomials():
+    rows, cols = 7, 9
+    n, rp, col = csr(G.grid(rows, cols))
+    dist, sigma = oracle.bfs(rp, col, 0)
+    for i in range(rows):
+        for j in range(cols):
+            assert dist[i * cols + j] == i + j
+            assert int(sigma[i * cols + j]) == comb(i + j, i)
+
+
+def test_sigma_near_uint64_limit_and_overflow():
+    gold = {(i, j): s for i, j, s in read_golden("binomial_grid_sigma.txt")}
+    n, rp, col = csr(G.grid(34, 35))
+    _, sigma = oracle.bfs(rp, col, 0)
+    assert int(sigma[33 * 35 + 33]) == gold[(33, 33)]
+    assert int(sigma[33 * 35 + 34]) == gold[(33, 34)]
+    assert gold[(34, 34)] >= 2 ** 64
+    n, rp, col = csr(G.grid(35, 35))
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.bfs(rp, col, 0)
+    assert e.value.rc == oracle.ERR_OVERFLOW
+
+
+def test_sigma_hypercube_factorials():
+    d = 6
+    n, rp, col = csr(G.hypercube(d))
+    dist, sigma = oracle.bfs(rp, col, 0)
+    for x in range(n):
+        pc = bin(x).count("1")
+        assert dist[x] == pc and int(sigma[x]) == factorial(pc)
+
+
+def test_sigma_trees_and_bipartite():
+    n, rp, col = csr(G.random_tree(200, 5))
+    for s in (0, 17, 199):
+        dist, sigma = oracle.bfs(rp, col, s)
+        assert np.all(sigma == 1) and np.all(dist >= 0)
+    a, b = 4, 7
+    n, rp, col = csr(G.complete_bipartite(a, b))
+    dist, sigma = oracle.bfs(rp, col, 0)           # from side A
+    assert np.all(sigma[1:a] == b) and np.all(dist[1:a] == 2)
+    dist, sigma = oracle.bfs(rp, col, a)           # from side B
+    assert np.all(sigma[a + 1:] == a) and np.all(dist[a + 1:] == 2)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_sssp_bruteforce_small(seed):
+    g = G.gnp(10, 0.3 + 0.05 * seed, 100 + seed)
+    n, rp, col = csr(g)
+    for s in range(n):
+        dist, sigma = oracle.bfs(rp, col, s)
+        bd, bs = sssp_bruteforce(*g, s)
+        assert np.array_equal(dist, bd)
+        assert [int(x) for x in sigma] == [int(x) for x in bs]
+
+
+# ------------------------------------------------------------------ betweenness closed forms
+@pytest.mark.parametrize("n", [2, 3, 8, 31])
+def test_path(n):
+    c = exact(G.path(n))
+    i = np.arange(n)
+    assert np.array_equal(c, (i * (n - 1 - i)).astype(float))
+
+
+@pytest.mark.parametrize("n", [3, 4, 25])
+def test_star(n):
+    c = exact(G.star(n))
+    assert c[0] == (n - 1) * (n - 2) / 2 and np.all(c[1:] == 0)
+
+
+@pytest.mark.parametrize("n", [5, 7, 12, 20, 21])
+def test_cycle(n):
+    c = exact(G.cycle(n))
+    r = n // 2
+    want = r * (r - 1) / 2 if n % 2 else (r - 1) ** 2 / 2
+    assert np.allclose(c, want, rtol=1e-13, atol=0)
+
+
+def test_complete_and_bipartite():
+    assert np.all(exact(G.complete(9)) == 0)
+    a, b = 3, 5
+    c = exact(G.complete_bipartite(a, b))
+    assert np.allclose(c[:a], comb(b, 2) / a, rtol=1e-14)
+    assert np.allclose(c[a:], comb(a, 2) / b, rtol=1e-14)
+
+
+def test_hypercube_q4():
+    c = exact(G.hypercube(4))
+    assert np.allclose(c, 8.5, rtol=1e-14)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_trees_component_formula(seed):
+    n = 300
+    g = G.random_tree(n, seed)
+    c = exact(g)
+    adj = [[] for _ in range(n)]
+    for a, b in zip(g[1].tolist(), g[2].tolist()):
+        adj[a].append(b)
+        adj[b].append(a)
+    # c(v) = [(n-1)^2 - sum_i s_i^2] / 2 over the components of T - v
+    for v in range(0, n, 7):
+        sizes = []
+        for start in adj[v]:
+            seen, stack = {v, start}, [start]
+            while stack:
+                x = stack.pop()
+                for y in adj[x]:
+                    if y not in seen:
+                        seen.add(y)
+                        stack.append(y)
+            sizes.append(len(seen) - 1)
+        assert c[v] == ((n - 1) ** 2 - sum(s * s for s in sizes)) / 2
+
+
+# ------------------------------------------------------------------ brute force on tiny graphs
+def _close(c, ref):
+    ref = np.array([float(x) for x in ref])
+    return np.allclose(c, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_all_labelled_graphs_on_5_vertices():
+    for mask in range(1 << 10):
+        g = G.from_mask(5, mask)
+        assert _close(exact(g), betweenness_bruteforce(*g)), mask
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_random_small_graphs_bruteforce(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(6, 13))
+    kind = seed % 4
+    if kind == 0:
+        g = G.gnp(n, float(rng.uniform(0.15, 0.5)), seed)
+    elif kind == 1:
+        g = G.random_tree(n, seed)
+    elif kind == 2:
+        g = G.gnp(n, 0.85, seed)                                # near-complete
+    else:
+        g = G.disjoint_union(G.gnp(n // 2, 0.5, seed), G.gnp(n - n // 2, 0.4, seed + 1))
+    assert _close(exact(g), betweenness_bruteforce(*g))
+
+
+def test_single_source_dependencies_bruteforce():
+    # delta_s(v) = sum_t sigma_st(v)/sigma_st, checked one source at a time.
+    from bruteforce import adjacency, enumerate_shortest_paths
+    g = G.gnp(11, 0.35, 9)
+    n, rp, col = csr(g)
+    adj = adjacency(*g)
+    for s in range(n):
+        delta = oracle.dependencies(rp, col, s)
+        ref = [Fraction(0)] * n
+        for t in range(n):
+            if t == s:
+                continue
+            ps = enumerate_shortest_paths(adj, s, t)
+            for p in ps:
+                for x in p[1:-1]:
+                    ref[x] += Fraction(1, len(ps))
+        ref[s] = delta[s]  # delta_s(s) is not a betweenness term
+        assert _close(delta, ref)
+
+
+# ------------------------------------------------------------------ invariant
+def pair_distance_sum(n, rp, col):
+    tot = 0
+    for s in range(n):
+        dist, _ = oracle.bfs(rp, col, s)
+        r = dist[dist > 0]
+        tot += int(np.sum(r - 1))
+    return tot / 2
+
+
+@pytest.mark.parametrize("graph", [G.gnp(120, 0.05, 4), G.grid(9, 13), G.random_tree(150, 8),
+                                   G.disjoint_union(G.cycle(30), G.gnp(60, 0.1, 5), G.star(9))])
+def test_sum_invariant(graph):
+    n, rp, col = csr(graph)
+    c = oracle.betweenness_exact(rp, col)
+    want = pair_distance_sum(n, rp, col)
+    assert math.isclose(c.sum(), want, rel_tol=1e-12)
+
+
+def test_sum_invariant_generated_er():
+    n, rp, col = oracle.generate("er", 600, 11, avg_deg=6.0)
+    c = oracle.betweenness_exact(rp, col)
+    assert math.isclose(c.sum(), pair_distance_sum(n, rp, col), rel_tol=1e-12)
+
+
+# ------------------------------------------------------------------ sampler and sampled estimate
+def test_sampler_properties():
+    n, k = 5000, 300
+    src = oracle.sample_sources(n, 2, k)
+    assert len(src) == k and np.all(np.diff(src) > 0) and src[0] >= 0 and src[-1] < n
+    keys = np.array([oracle.stream(2, v) for v in range(n)], dtype=np.uint64)
+    chosen = np.zeros(n, bool)
+    chosen[src] = True
+    assert keys[chosen].max() < keys[~chosen].min()   # exactly the k smallest keys
+    assert np.array_equal(oracle.sample_sources(n, 2, n), np.arange(n))
+    assert not np.array_equal(src, oracle.sample_sources(n, 3, k))
+
+
+def test_sampler_uniform_inclusion():
+    n, k, seeds = 40, 10, 3000
+    counts = np.zeros(n)
+    for s in range(seeds):
+        counts[oracle.sample_sources(n, s + 1000, k)] += 1
+    p = k / n
+    sd = math.sqrt(seeds * p * (1 - p))
+    assert np.all(np.abs(counts - seeds * p) < 5 * sd)
+    chi2 = float(np.sum((counts - seeds * p) ** 2 / (seeds * p)))
+    assert chi2 < n + 6 * math.sqrt(2 * n)
+
+
+def test_sampled_k_equals_n_is_exact():
+    n, rp, col = oracle.generate("er", 300, 5, avg_deg=5.0)
+    assert np.array_equal(oracle.betweenness_sampled(rp, col, 99, n), oracle.betweenness_exact(rp, col))
+
+
+def test_sampled_estimator_is_unbiased():
+    n, rp, col = oracle.generate("er", 200, 21, avg_deg=6.0)
+    c = oracle.betweenness_exact(rp, col)
+    runs = np.stack([oracle.betweenness_sampled(rp, col, seed, 20) for seed in range(200)])
+    mean, se = runs.mean(0), runs.std(0, ddof=1) / math.sqrt(len(runs))
+    mask = c > 0
+    z = np.abs(mean[mask] - c[mask]) / np.maximum(se[mask], 1e-12)
+    assert np.mean(z < 4) > 0.99
+    assert abs(runs.sum(1).mean() - c.sum()) < 4 * runs.sum(1).std(ddof=1) / math.sqrt(len(runs))
+
+
+@pytest.mark.slow
+def test_sampled_top_ranks_close_to_exact():
+    n, rp, col = oracle.generate("ba", 10000, 1, m0=8)
+    c = oracle.betweenness_exact(rp, col)
+    ch = oracle.betweenness_sampled(rp, col, 2, 256)
+    top = set(np.argsort(-c)[:10].tolist())
+    top_h = set(np.argsort(-ch)[:10].tolist())
+    assert len(top & top_h) >= 6
+
+
+# ------------------------------------------------------------------ generators (Section 5)
+def check_canonical(n, rp, col):
+    assert rp[0] == 0 and rp[-1] == len(col) and np.all(np.diff(rp) >= 0)
+    src = np.repeat(np.arange(n), np.diff(rp))
+    assert np.all(src != col)
+    key = src.astype(np.int64) * n + col
+    assert np.all(np.diff(key) > 0)
+    rkey = col.astype(np.int64) * n + src
+    assert np.array_equal(np.sort(rkey), key)
+
+
+def test_er_edge_count_and_canonical():
+    n, d = 2000, 8.0
+    N, p = n * (n - 1) // 2, d / (n - 1)
+    ms = []
+    for seed in range(1, 9):
+        eu, ev = oracle.gen_er(n, d, seed)
+        assert np.all(eu > ev)                       # pairs u > v, never repeated
+        t = eu.astype(np.int64) * (eu - 1) // 2 + ev
+        assert np.all(np.diff(t) > 0)
+        ms.append(len(eu))
+    sd = math.sqrt(N * p * (1 - p))
+    assert all(abs(m - N * p) < 4 * sd for m in ms)
+    nn, rp, col = oracle.generate("er", n, 1, avg_deg=d)
+    check_canonical(nn, rp, col)
+    assert len(col) == 2 * oracle.gen_er(n, d, 1)[0].size
+
+
+def test_er_pair_inclusion_uniform():
+    # every pair is an edge independently with probability p (tests the skip logic,
+    # including the chunk boundary: n = 1500 has 1,124,250 > 2^20 pairs)
+    n, p, seeds = 24, 0.3, 2500
+    N = n * (n - 1) // 2
+    counts = np.zeros(N)
+    for s in range(seeds):
+        eu, ev = oracle.gen_er(n, p * (n - 1), s + 77)
+        counts[eu.astype(np.int64) * (eu - 1) // 2 + ev] += 1
+    sd = math.sqrt(seeds * p * (1 - p))
+    assert np.all(np.abs(counts - seeds * p) < 5 * sd)
+    # chunk boundary: the density of pairs just below and above 2^20 matches p
+    n2 = 1500
+    p2 = 0.01
+    hits = np.zeros(2)
+    for s in range(40):
+        eu, ev = oracle.gen_er(n2, p2 * (n2 - 1), s)
+        t = eu.astype(np.int64) * (eu - 1) // 2 + ev
+        hits[0] += np.sum((t >= (1 << 20) - 50000) & (t < (1 << 20)))
+        hits[1] += np.sum((t >= (1 << 20)) & (t < (1 << 20) + 50000))
+    for h in hits:
+        assert abs(h - 40 * 50000 * p2) < 5 * math.sqrt(40 * 50000 * p2)
+
+
+def test_er_complete_and_empty():
+    eu, ev = oracle.gen_er(6, 5.0, 1)
+    assert len(eu) == 15
+    assert len(oracle.gen_er(6, 0.0, 1)[0]) == 0
+
+
+def test_ba_attachment_distribution():
+    # n=4, m0=1: the Batagelj-Brandes array draws r_1 in [0,2], r_2 in [0,4], r_3 in
+    # [0,6]; enumerate the 105 equally likely draw sequences and compare the law of
+    # the resulting edge list with the generator over many seeds.
+    from collections import Counter
+    law = Counter()
+    for r1 in range(3):
+        for r2 in range(5):
+            for r3 in range(7):
+                M = [0, 0]
+                for e, r in ((1, r1), (2, r2), (3, r3)):
+                    M.append(e)
+                    M.append(M[r])
+                law[tuple(M)] += 1
+    seeds = 21000
+    seen = Counter()
+    for s in range(seeds):
+        eu, ev = oracle.gen_ba(4, 1, s)
+        M = []
+        for a, b in zip(eu.tolist(), ev.tolist()):
+            M += [a, b]
+        seen[tuple(M)] += 1
+    assert set(seen) <= set(law)
+    chi2 = sum((seen[k] - seeds * w / 105) ** 2 / (seeds * w / 105) for k, w in law.items())
+    dof = len(law) - 1
+    assert chi2 < dof + 6 * math.sqrt(2 * dof)
+
+
+def test_ba_structure():
+    n, m0 = 5000, 4
+    eu, ev = oracle.gen_ba(n, m0, 3)
+    assert len(eu) == n * m0
+    assert np.array_equal(eu, np.repeat(np.arange(n), m0))
+    assert np.all(ev <= eu)                              # attaches to earlier (or itself)
+    nn, rp, col = oracle.generate("ba", n, 3, m0=m0)
+    check_canonical(nn, rp, col)
+    deg = np.diff(rp)
+    assert np.all(deg[1:] >= 1) and len(col) <= 2 * n * m0
+    assert deg.max() > 20 * m0                         # heavy tail: hubs exist
+
+
+def test_rmat_quadrant_frequencies():
+    scale, ef, a, b, c = 12, 16, 0.57, 0.19, 0.19
+    eu, ev = oracle.gen_rmat(scale, ef, a, b, c, 5)
+    assert len(eu) == ef << scale and eu.max() < 1 << scale and ev.max() < 1 << scale
+    E = len(eu)
+    for bit in (scale - 1, 0):
+        ru, rv = (eu >> bit) & 1, (ev >> bit) & 1
+        for (x, y), p in (((0, 0), a), ((0, 1), b), ((1, 0), c), ((1, 1), 1 - a - b - c)):
+            f = np.sum((ru == x) & (rv == y))
+            assert abs(f - E * p) < 5 * math.sqrt(E * p * (1 - p))
+    n, rp, col = oracle.generate("rmat", 10, 1)
+    check_canonical(n, rp, col)
