@@ -1,0 +1,226 @@
+/*
+ * nk.h - C ABI of the GB300 betweenness-centrality library (libnk.so).
+ *
+ * Betweenness of a vertex v in an undirected, unweighted, simple graph G = (V, E):
+ *     c(v) = sum over unordered pairs {s,t}, s != v != t, sigma_st > 0, of
+ *            sigma_st(v) / sigma_st,
+ * where sigma_st counts shortest s-t paths and sigma_st(v) those through v.  It is
+ * computed by Brandes' algorithm [Bra01] (Section 3.2 and Table 1 of the NetworKit
+ * paper, "betweenness", O(nm) time): per source s, a BFS (unweighted graphs, Section
+ * 3.4) that counts sigma, then the dependency accumulation
+ *     delta_s(v) = sum_{w : v is a predecessor of w} sigma_sv / sigma_sw * (1 + delta_s(w)),
+ * and the dependencies of all sources are summed (Section 3.2).  The sampled
+ * estimate (Section 3.2, after Geisberger et al.) sums the dependencies of k sources
+ * drawn uniformly without replacement and scales the sum by n/k.
+ *
+ * Conventions shared by every call:
+ *   - Return value: NK_OK (0) or a negative NK_ERR_* code; never aborts.  The
+ *     thread-local nk_last_error() describes the last failure of the calling thread.
+ *   - Vertex ids and CSR offsets are int32; n >= 1 and the arc count A < 2^31.
+ *   - Graphs are immutable, canonical CSR resident in GPU memory, owned by the library
+ *     until nk_graph_free().  Canonical: for every vertex the neighbour list is sorted
+ *     ascending, holds no duplicate and no self-loop, and u in N(v) <=> v in N(u).
+ *   - Host pointers unless a flag says otherwise.  Output buffers are owned by the
+ *     caller.  Calls are synchronous (they return after results are written) and are
+ *     ordered on the stream set by nk_set_stream (default: the legacy default stream).
+ *   - Scores are raw (no normalisation): each unordered pair counts once.
+ */
+#ifndef NK_H
+#define NK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define NK_OK 0
+#define NK_PENDING 1          /* serving: request admitted or queued, not finished */
+#define NK_ERR_ARG (-1)       /* invalid argument (null pointer, k outside [1,n], ...) */
+#define NK_ERR_GRAPH (-2)     /* CSR not canonical / ids out of range */
+#define NK_ERR_NOMEM (-3)     /* device memory (or the serving budget) exhausted */
+#define NK_ERR_OVERFLOW (-4)  /* a shortest-path count sigma exceeded 2^64 - 1 */
+#define NK_ERR_CUDA (-5)      /* a CUDA runtime call failed */
+#define NK_ERR_TIMEOUT (-6)   /* a bounded device-side wait ran out */
+#define NK_ERR_SHUTDOWN (-7)  /* serving: server is shutting down */
+
+/* ---------------------------------------------------------------- graph construction */
+#define NK_CSR_VALIDATE 1u     /* check canonical form; NK_ERR_GRAPH if it is not */
+#define NK_CSR_CANONICALISE 2u /* symmetrise, drop self-loops, sort, dedupe on the GPU */
+#define NK_CSR_DEVICE_PTRS 4u  /* input arrays are device pointers */
+
+typedef struct nk_graph nk_graph;
+
+/* Builds a graph from CSR arrays row_ptr[n+1] (row_ptr[0] = 0, row_ptr[n] = n_arcs) and
+ * col[n_arcs].  Flags: none = trust the caller (must already be canonical; ids are
+ * still range-checked on the GPU), NK_CSR_VALIDATE, or NK_CSR_CANONICALISE (any
+ * adjacency, e.g. one direction per edge, duplicates, self-loops).  The arrays are
+ * copied; the caller keeps ownership.  Graph structure: Section 2.3 (adjacency
+ * structure with O(n+m) memory; here an immutable int32 CSR). */
+int nk_graph_from_csr(int32_t n, const int32_t *row_ptr, const int32_t *col, int64_t n_arcs,
+                      uint32_t flags, nk_graph **out);
+
+/* Builds the canonical graph of an undirected edge list (u[i], v[i]), i < m: both
+ * directions, self-loops dropped, duplicates removed; the CSR is built on the GPU.
+ * Flags: NK_CSR_DEVICE_PTRS only.  Out-of-range ids give NK_ERR_GRAPH. */
+int nk_graph_from_edges(int32_t n, int64_t m, const int32_t *u, const int32_t *v,
+                        uint32_t flags, nk_graph **out);
+
+/* Seeded generators of Section 5 (Table 2), run on the GPU, followed by the canonical
+ * CSR build.  Random numbers: SplitMix64 (Steele, Lea, Flood 2014) as a counter-based
+ * generator, stream(seed, i) = mix64(seed + (i+1) * 0x9E3779B97F4A7C15).
+ *   NK_GEN_ER   n_or_scale = n, params[0] = average degree d (p = d/(n-1)); G(n,p) by
+ *               Batagelj-Brandes geometric skipping in chunks of 2^20 vertex pairs.
+ *   NK_GEN_BA   n_or_scale = n, params[0] = m0 edges per vertex; Batagelj-Brandes
+ *               linear preferential attachment.
+ *   NK_GEN_RMAT n_or_scale = scale (n = 2^scale), params = {edge_factor, a, b, c};
+ *               edge_factor * 2^scale raw edges (Chakrabarti et al.).
+ * The result is identical, byte for byte, on every run with the same arguments. */
+#define NK_GEN_ER 1
+#define NK_GEN_BA 2
+#define NK_GEN_RMAT 3
+int nk_graph_generate(int kind, const double *params, int32_t n_or_scale, uint64_t seed,
+                      nk_graph **out);
+
+/* n and the number of arcs A (= 2 * undirected edges). */
+int nk_graph_info(const nk_graph *g, int32_t *n, int64_t *n_arcs);
+
+/* Copies the canonical CSR to host arrays row_ptr[n+1] and col[A]. */
+int nk_graph_export_csr(const nk_graph *g, int32_t *row_ptr, int32_t *col);
+
+/* Frees the graph and its cached device workspace.  NK_ERR_ARG if serving requests on
+ * it are still pending (the graph is then not freed). */
+int nk_graph_free(nk_graph *g);
+
+/* ---------------------------------------------------------------- sampler (Section 3.2) */
+/* k distinct sources, uniform without replacement: the k vertices with the smallest
+ * (stream(seed, v), v); written to src[k] in ascending id order.  1 <= k <= n.
+ * flags: NK_RUN_DEVICE_PTRS makes src a device pointer. */
+int nk_sample_sources(int32_t n, uint64_t seed, int32_t k, int32_t *src, uint32_t flags);
+
+/* ---------------------------------------------------------------- single-source sweep */
+/* Forward BFS from s (Section 3.4): dist[v] = hops from s (-1 unreachable), sigma[v] =
+ * number of shortest s-v paths.  Host arrays of n entries.  NK_ERR_OVERFLOW if some
+ * sigma exceeds 2^64 - 1 (outputs are then unspecified). */
+int nk_sssp(const nk_graph *g, int32_t s, int32_t *dist, uint64_t *sigma);
+
+/* ---------------------------------------------------------------- betweenness */
+#define NK_MODE_AUTO 0       /* batched where it fits, per-source otherwise */
+#define NK_MODE_PER_SOURCE 1 /* plain per-source kernel (one BFS tree at a time) */
+#define NK_MODE_BATCHED 2    /* bitset multi-source kernel, `batch` sources per launch */
+
+#define NK_DIR_AUTO 0        /* direction-optimising: switch by alpha */
+#define NK_DIR_TOP_DOWN 1    /* every level top-down (push from the frontier) */
+#define NK_DIR_BOTTOM_UP 2   /* every level bottom-up (pull into unvisited vertices) */
+
+#define NK_RUN_DEVICE_PTRS 1u  /* scores (and src) are device pointers */
+#define NK_RUN_TIME_KERNELS 2u /* record per-launch durations of the sweep kernel */
+
+typedef struct nk_run_opts {
+    int32_t mode;      /* NK_MODE_* */
+    int32_t batch;     /* batched mode: sources per batch, 64/128/256; 0 = autotuned */
+    int32_t tpv;       /* per-source mode: threads per vertex 1..32 (power of 2); 0 = auto */
+    int32_t direction; /* NK_DIR_* */
+    double alpha;      /* bottom-up when alpha * (frontier arcs) > (unvisited arcs); 0 = auto */
+    uint32_t flags;    /* NK_RUN_* */
+    int32_t reserved[7];
+} nk_run_opts;
+
+/* Statistics of the last betweenness call made by this thread. */
+typedef struct nk_run_stats {
+    int32_t mode;            /* mode actually used */
+    int32_t batch;           /* sources per batch used (1 for per-source) */
+    int32_t tpv;
+    int32_t max_depth;       /* deepest BFS level seen */
+    int64_t launches;        /* sweep-kernel launches */
+    double kernel_ms;        /* sum of sweep-kernel durations (CUDA events), if timed */
+    int64_t td_levels;       /* levels run top-down / bottom-up */
+    int64_t bu_levels;
+    double alpha;
+} nk_run_stats;
+
+/* Exact betweenness: all n sources, scores[n] = (1/2) sum_s delta_s(v). */
+int nk_betweenness_exact(const nk_graph *g, double *scores);
+
+/* Sampled betweenness: k sources from nk_sample_sources(n, seed, k), scores[n] =
+ * n/(2k) * sum_{s in S} delta_s(v).  1 <= k <= n. */
+int nk_betweenness_sampled(const nk_graph *g, uint64_t seed, int32_t k, double *scores);
+
+/* Sampled betweenness with explicit options (opts may be NULL for defaults). */
+int nk_betweenness_sampled_opts(const nk_graph *g, uint64_t seed, int32_t k, double *scores,
+                                const nk_run_opts *opts);
+
+/* scores[n] = scale * sum_{s in src} delta_s(v) over an explicit list of k distinct
+ * sources (k >= 1).  The general entry point behind the two above. */
+int nk_betweenness_sources(const nk_graph *g, const int32_t *src, int32_t k, double scale,
+                           double *scores, const nk_run_opts *opts);
+
+/* Stats of the calling thread's last betweenness call. */
+int nk_last_run_stats(nk_run_stats *out);
+
+/* Autotuner: times candidate (batch, alpha, tpv) settings on a short sample of the
+ * graph's own sources and writes the fastest into *best (cached per graph; later
+ * calls with batch/alpha = 0 use it). */
+int nk_autotune(const nk_graph *g, uint64_t seed, int32_t k, nk_run_opts *best);
+
+/* ---------------------------------------------------------------- serving runtime */
+typedef struct nk_server nk_server;
+typedef int64_t nk_req;
+
+typedef struct nk_server_opts {
+    double mem_budget_bytes; /* device bytes for per-request state; 0 = 60% of free */
+    int32_t max_inflight;    /* requests on the GPU at once (streams); 0 = 8 */
+    int32_t batch;           /* sources per batch for served requests; 0 = 64 */
+    double timeout_s;        /* bound on device-side waits; 0 = 10 s */
+    int32_t reserved[8];
+} nk_server_opts;
+
+typedef struct nk_server_stats {
+    int64_t submitted, completed, failed, rejected;
+    double p50_ms, p99_ms, max_ms;   /* submit-to-completion latency of completed requests */
+    double busy_s;                   /* wall time with at least one request on the GPU */
+    double edges_x_sources;          /* sum over completed requests of m * k */
+    int64_t peak_inflight;
+    double peak_bytes;
+} nk_server_stats;
+
+int nk_server_create(const nk_server_opts *opts, nk_server **out);
+/* Waits for pending requests, then frees the server. */
+void nk_server_destroy(nk_server *srv);
+
+/* Queues a sampled-betweenness request (graph, seed, k).  `scores` (n doubles, host)
+ * must stay valid until nk_serve_poll returns something other than NK_PENDING.
+ * Admission is by the device-memory budget; requests larger than the whole budget are
+ * rejected with NK_ERR_NOMEM. */
+int nk_serve_submit(nk_server *srv, const nk_graph *g, uint64_t seed, int32_t k,
+                    double *scores, nk_req *id);
+
+/* NK_PENDING while queued or running; then NK_OK or the request's error code. */
+int nk_serve_poll(nk_server *srv, nk_req id);
+
+/* Blocks until request id is finished (or timeout_s elapses: NK_PENDING). */
+int nk_serve_wait(nk_server *srv, nk_req id, double timeout_s);
+
+int nk_server_get_stats(nk_server *srv, nk_server_stats *out);
+
+/* ---------------------------------------------------------------- misc */
+/* Stream used by every later call of this process (a cudaStream_t); NULL = default. */
+int nk_set_stream(void *stream);
+
+/* Bound, in nanoseconds, on every device-side wait (grid barrier); default 10 s. */
+int nk_set_wait_limit_ns(uint64_t ns);
+
+/* Failure-detection self test: launches a kernel whose wait on a flag that nothing
+ * sets runs out after limit_ns; returns NK_ERR_TIMEOUT when the bounded wait works
+ * (and the CUDA context stays usable). */
+int nk_selftest_wait_timeout(uint64_t limit_ns);
+
+const char *nk_last_error(void);
+const char *nk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NK_H */

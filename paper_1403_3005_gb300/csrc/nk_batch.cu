@@ -1,0 +1,650 @@
+// Batched multi-source betweenness: B = 64*W sources share one persistent cooperative
+// launch.  The paper parallelises Brandes' algorithm over sources with one dependency
+// array per thread, summed at the end (Section 3.2); on the GPU the sources of a batch
+// instead share every pass over the CSR, so the adjacency of a level is read once for
+// all B shortest-path trees.
+//
+// State of one batch, all in HBM (b = source slot 0..B-1, q = word 0..W-1):
+//   F_d[v][q]   bitset of the sources for which v is at BFS level d (one slab per
+//               level, kept for the backward sweep)
+//   vis[v][q]   union of F_0..F_d
+//   sp[v][b]    sigma_b(v) (uint64) during the forward sweep; replaced by
+//               psi_b(v) = (1 + delta_b(v)) / sigma_b(v) (double) in the backward sweep
+//   queue       vertices of the levels found top-down (levels found bottom-up are
+//               iterated by scanning F_d)
+// Forward level d, either
+//   bottom-up  every vertex w with unvisited sources u = act & ~vis[w] gathers F_d of
+//              its neighbours (one warp per vertex, lanes over neighbours); for every
+//              neighbour c with F_d[c] & u != 0 the lanes switch to one lane per source
+//              bit and add sigma_b(c) (the sigma row of c is contiguous, so the gather
+//              reads only the sectors of the sources that need it);
+//              F_{d+1}[w] = the bits whose sum is non-zero;  or
+//   top-down   (a) every frontier vertex v pushes m = F_d[v] & ~vis[c] into F_{d+1}[c]
+//              (atomicOr) and queues c once per level; (b) every queued vertex w pulls
+//              sigma for exactly its new bits F_{d+1}[w], as above.  sigma is never
+//              updated atomically, so sp needs no zeroing.
+// Backward level d (deepest first): every v with F_d[v] != 0 gathers, per source bit b
+// of F_d[v], acc_b = sum of psi_b(c) over neighbours c with bit b in F_{d+1}[c]; then
+// delta_b(v) = sigma_b(v) * acc_b (Brandes' recurrence with sigma_v factored out), psi
+// overwrites sigma, and scores[v] += sum_b delta_b(v).
+// Bottom-up is chosen when alpha * (arcs of frontier vertices) > (arcs of vertices not
+// yet visited by every source).  A BFS deeper than the level slabs aborts the batch
+// before its backward sweep (scores untouched); the host re-runs those sources with
+// the per-source form.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "nk_device.cuh"
+#include "nk_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace nk {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kErrDepth = 100;  // internal status: BFS deeper than the level slabs
+constexpr unsigned FULL = 0xffffffffu;
+
+struct BArgs {
+    int32_t n;
+    int64_t A;
+    const int32_t *rp, *col;
+    const int32_t *src;
+    int32_t nsrc;
+    int32_t lcap;                // levels 0..lcap may be non-empty; slabs 0..lcap+1
+    unsigned long long *F;       // [lcap+2][n][W]
+    unsigned long long *vis;     // [n][W]
+    unsigned long long *sp;      // [n][B]
+    int32_t *qmark;              // [n] last level a vertex was queued for
+    int32_t *queue;              // [qcap]
+    int64_t qcap;
+    int32_t *vcnt;               // [lcap+3] vertices with F_d != 0
+    int32_t *qcnt;               // [lcap+3] queue entries of level d
+    int32_t *qoff;               // [lcap+3] start of level d in queue, -1 if not queued
+    unsigned long long *mfv;     // [lcap+3] sum of degrees of the level-d vertices
+    unsigned long long *dmu;     // [lcap+3] degrees of vertices completed at level d
+    double *scores;
+    Ctrl *ctrl;
+    uint64_t limit_ns;
+    double alpha;
+    int dir;
+};
+
+template <int W> struct Bits {
+    unsigned long long w[W];
+};
+
+template <int W> __device__ __forceinline__ Bits<W> load_bits(const unsigned long long *p)
+{
+    Bits<W> r;
+    if constexpr (W == 1) {
+        r.w[0] = __ldcg(p);
+    } else {
+#pragma unroll
+        for (int q = 0; q < W; q += 2) {
+            const ulonglong2 x = __ldcg(reinterpret_cast<const ulonglong2 *>(p + q));
+            r.w[q] = x.x;
+            r.w[q + 1] = x.y;
+        }
+    }
+    return r;
+}
+
+template <int W> __device__ __forceinline__ bool any_bits(const Bits<W> &b)
+{
+    unsigned long long o = 0;
+#pragma unroll
+    for (int q = 0; q < W; ++q) o |= b.w[q];
+    return o != 0;
+}
+
+template <int W> __device__ __forceinline__ Bits<W> shfl_bits(const Bits<W> &b, int src)
+{
+    Bits<W> r;
+#pragma unroll
+    for (int q = 0; q < W; ++q) r.w[q] = __shfl_sync(FULL, b.w[q], src);
+    return r;
+}
+
+template <int W> __device__ __forceinline__ Bits<W> andnot(const Bits<W> &x, const Bits<W> &y)
+{
+    Bits<W> r;
+#pragma unroll
+    for (int q = 0; q < W; ++q) r.w[q] = x.w[q] & ~y.w[q];
+    return r;
+}
+
+__device__ __forceinline__ int deg_of(const int32_t *rp, int v) { return __ldg(rp + v + 1) - __ldg(rp + v); }
+
+// Slot k of a lane covers source bit 32k + lane: word k/2, bit 32(k&1) + lane.
+template <int W> __device__ __forceinline__ bool has_slot(const Bits<W> &b, int k, int lane)
+{
+    return (b.w[k >> 1] >> (((k & 1) << 5) + lane)) & 1ull;
+}
+
+// For the warp's vertex with adjacency [beg, end): per source slot, the sum of sp over
+// the neighbours c whose Fsel[c] & tgt holds that source bit; uint64 sums (sigma, with
+// carry detection) or double sums (psi).  Lanes over neighbours find the relevant
+// ones; then lanes over source bits read the contiguous sp rows, two neighbours per
+// round so that their loads are in flight together.
+template <int W, bool PSI>
+__device__ __forceinline__ void gather(const BArgs &a, int beg, int end,
+                                       const unsigned long long *Fsel, const Bits<W> &tgt,
+                                       unsigned long long (&acc)[2 * W], double (&facc)[2 * W],
+                                       bool &ovf)
+{
+    constexpr int B = 64 * W;
+    const int lane = threadIdx.x & 31;
+    for (int base = beg; base < end; base += 32) {
+        const int j = base + lane;
+        int c = 0;
+        Bits<W> f;
+#pragma unroll
+        for (int q = 0; q < W; ++q) f.w[q] = 0;
+        if (j < end) {
+            c = __ldg(a.col + j);
+            const Bits<W> fc = load_bits<W>(Fsel + (size_t)c * W);
+#pragma unroll
+            for (int q = 0; q < W; ++q) f.w[q] = fc.w[q] & tgt.w[q];
+        }
+        unsigned rel = __ballot_sync(FULL, any_bits<W>(f));
+        while (rel) {
+            const int s0 = __ffs(rel) - 1;
+            rel &= rel - 1;
+            int s1 = s0;
+            const bool two = rel != 0;
+            if (two) {
+                s1 = __ffs(rel) - 1;
+                rel &= rel - 1;
+            }
+            const int c0 = __shfl_sync(FULL, c, s0);
+            const int c1 = __shfl_sync(FULL, c, s1);
+            const Bits<W> f0 = shfl_bits<W>(f, s0);
+            const Bits<W> f1 = shfl_bits<W>(f, s1);
+            const unsigned long long *r0 = a.sp + (size_t)c0 * B + lane;
+            const unsigned long long *r1 = a.sp + (size_t)c1 * B + lane;
+            unsigned long long x0[2 * W], x1[2 * W];
+#pragma unroll
+            for (int k = 0; k < 2 * W; ++k) {
+                x0[k] = has_slot<W>(f0, k, lane) ? __ldcg(r0 + 32 * k) : 0ull;
+                x1[k] = (two && has_slot<W>(f1, k, lane)) ? __ldcg(r1 + 32 * k) : 0ull;
+            }
+#pragma unroll
+            for (int k = 0; k < 2 * W; ++k) {
+                if constexpr (PSI) {
+                    facc[k] += __longlong_as_double((long long)x0[k]);
+                    facc[k] += __longlong_as_double((long long)x1[k]);
+                } else {
+                    const unsigned long long y = acc[k] + x0[k];
+                    const unsigned long long z = y + x1[k];
+                    ovf |= (y < acc[k]) | (z < y);
+                    acc[k] = z;
+                }
+            }
+        }
+    }
+}
+
+template <int W> __device__ __forceinline__ Bits<W> nonzero_bits(const unsigned long long (&acc)[2 * W])
+{
+    Bits<W> r;
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+        const unsigned lo = __ballot_sync(FULL, acc[2 * q] != 0ull);
+        const unsigned hi = __ballot_sync(FULL, acc[2 * q + 1] != 0ull);
+        r.w[q] = (unsigned long long)lo | ((unsigned long long)hi << 32);
+    }
+    return r;
+}
+
+struct BlockCnt {
+    int v;
+    unsigned long long mf, dmu;
+};
+
+// Vertex w joined level d+1 for the sources in nb (vold = its visited set before):
+// writes its sigma row and visited set (and F_{d+1} when Fn is given), and counts it.
+// Called by the whole warp with warp-uniform arguments.
+template <int W>
+__device__ __forceinline__ void settle(const BArgs &a, int w, const Bits<W> &vold, const Bits<W> &nb,
+                                       const Bits<W> &act, const unsigned long long (&acc)[2 * W],
+                                       unsigned long long *Fn, BlockCnt *bc)
+{
+    constexpr int B = 64 * W;
+    const int lane = threadIdx.x & 31;
+    unsigned long long *row = a.sp + (size_t)w * B + lane;
+#pragma unroll
+    for (int k = 0; k < 2 * W; ++k)
+        if (has_slot<W>(nb, k, lane)) row[32 * k] = acc[k];
+    bool full = true;
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+        const unsigned long long nv = vold.w[q] | nb.w[q];
+        full &= nv == act.w[q];
+        if (lane == q) {
+            a.vis[(size_t)w * W + q] = nv;
+            if (Fn) Fn[(size_t)w * W + q] = nb.w[q];
+        }
+    }
+    if (lane == 0) {
+        const unsigned long long dg = (unsigned long long)deg_of(a.rp, w);
+        atomicAdd(&bc->v, 1);
+        atomicAdd(&bc->mf, dg);
+        if (full) atomicAdd(&bc->dmu, dg);
+    }
+}
+
+// Calls fn(v) with the whole warp for every vertex of a level: the queued entries
+// queue[qo, qo+nq) or, if qo < 0, every v with Fl[v] != 0 (scanned 32 at a time).
+template <int W, class Fn>
+__device__ __forceinline__ void for_level(const BArgs &a, int qo, int nq,
+                                          const unsigned long long *Fl, Fn fn)
+{
+    const int lane = threadIdx.x & 31;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    if (qo >= 0) {
+        for (long long i = wid; i < nq; i += nw) fn(__ldcg(a.queue + qo + i));
+    } else {
+        for (long long base = wid * 32; base < a.n; base += nw * 32) {
+            const long long v = base + lane;
+            const bool nz = v < a.n && any_bits<W>(load_bits<W>(Fl + (size_t)v * W));
+            unsigned m = __ballot_sync(FULL, nz);
+            while (m) {
+                const int t = __ffs(m) - 1;
+                m &= m - 1;
+                fn((int)(base + t));
+            }
+        }
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
+{
+    constexpr int B = 64 * W;
+    __shared__ BlockCnt bc;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    const long long wid = tid >> 5, nw = nthr >> 5;
+    const size_t slab = (size_t)a.n * W;
+    Bits<W> act;
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+        const int left = a.nsrc - 64 * q;
+        act.w[q] = left >= 64 ? ~0ull : (left <= 0 ? 0ull : ((1ull << left) - 1));
+    }
+    bool ovf = false;
+
+    // ---- init: empty visited sets, F_0 and F_1, queue marks, level-0..2 counters
+    for (size_t i = tid; i < slab; i += nthr) {
+        a.vis[i] = 0;
+        a.F[i] = 0;
+        a.F[slab + i] = 0;
+    }
+    for (long long i = tid; i < a.n; i += nthr) a.qmark[i] = -1;
+    if (tid < 3) {
+        a.vcnt[tid] = 0;
+        a.qcnt[tid] = 0;
+        a.qoff[tid] = -1;
+        a.mfv[tid] = 0;
+        a.dmu[tid] = 0;
+    }
+    if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+    if (tid < a.nsrc) {
+        const int s = __ldg(a.src + tid);
+        const unsigned long long bit = 1ull << (tid & 63);
+        atomicOr(a.F + (size_t)s * W + (tid >> 6), bit);
+        atomicOr(a.vis + (size_t)s * W + (tid >> 6), bit);
+        a.sp[(size_t)s * B + tid] = 1ull;
+        a.queue[tid] = s;
+        atomicAdd(a.mfv, (unsigned long long)deg_of(a.rp, s));
+        if (a.nsrc == 1) a.dmu[0] = (unsigned long long)deg_of(a.rp, s);
+    }
+    if (tid == 0) {
+        a.vcnt[0] = a.nsrc;
+        a.qcnt[0] = a.nsrc;
+        a.qoff[0] = 0;
+    }
+    if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+
+    long long mu = a.A - (long long)__ldcg(a.dmu);
+    long long mf = (long long)__ldcg(a.mfv);
+    int d = 0, qo = 0, nq = a.nsrc, td = 0, bu = 0;
+    long long qtail = a.nsrc;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            bc.v = 0;
+            bc.mf = 0;
+            bc.dmu = 0;
+        }
+        if (tid == 0) {
+            a.vcnt[d + 2] = 0;
+            a.qcnt[d + 2] = 0;
+            a.mfv[d + 2] = 0;
+            a.dmu[d + 2] = 0;
+        }
+        {
+            unsigned long long *Fz = a.F + (size_t)(d + 2) * slab;
+            for (size_t i = tid; i < slab; i += nthr) Fz[i] = 0;
+        }
+        __syncthreads();
+        const unsigned long long *Fd = a.F + (size_t)d * slab;
+        unsigned long long *Fn = a.F + (size_t)(d + 1) * slab;
+        const bool use_bu = a.dir == NK_DIR_BOTTOM_UP ||
+                            (a.dir == NK_DIR_AUTO && a.alpha * (double)mf > (double)mu);
+        bool queued = false;
+        int nq1 = 0;
+        if (use_bu) {
+            // ---- bottom-up: every vertex with unvisited sources pulls from level d
+            for (long long base = wid * 32; base < a.n; base += nw * 32) {
+                const long long v = base + lane;
+                Bits<W> vv = act;
+                if (v < a.n) vv = load_bits<W>(a.vis + (size_t)v * W);
+                unsigned m = __ballot_sync(FULL, any_bits<W>(andnot<W>(act, vv)));
+                while (m) {
+                    const int t = __ffs(m) - 1;
+                    m &= m - 1;
+                    const int w = (int)(base + t);
+                    const Bits<W> vold = shfl_bits<W>(vv, t);
+                    const Bits<W> u = andnot<W>(act, vold);
+                    unsigned long long acc[2 * W];
+                    double facc[2 * W];
+#pragma unroll
+                    for (int k = 0; k < 2 * W; ++k) acc[k] = 0;
+                    gather<W, false>(a, __ldg(a.rp + w), __ldg(a.rp + w + 1), Fd, u, acc, facc, ovf);
+                    const Bits<W> nb = nonzero_bits<W>(acc);
+                    if (any_bits<W>(nb)) settle<W>(a, w, vold, nb, act, acc, Fn, &bc);
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                if (bc.v) atomicAdd(a.vcnt + d + 1, bc.v);
+                if (bc.mf) atomicAdd(a.mfv + d + 1, bc.mf);
+                if (bc.dmu) atomicAdd(a.dmu + d + 1, bc.dmu);
+            }
+            if (tid == 0) a.qoff[d + 1] = -1;
+            if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+        } else {
+            // ---- top-down (a): push the frontier's bits, queue each new vertex once
+            for_level<W>(a, qo, nq, Fd, [&](int v) {
+                const Bits<W> f = load_bits<W>(Fd + (size_t)v * W);
+                const int beg = __ldg(a.rp + v), end = __ldg(a.rp + v + 1);
+                for (int j = beg + lane; j < end; j += 32) {
+                    const int c = __ldg(a.col + j);
+                    const Bits<W> m = andnot<W>(f, load_bits<W>(a.vis + (size_t)c * W));
+                    if (!any_bits<W>(m)) continue;
+#pragma unroll
+                    for (int q = 0; q < W; ++q)
+                        if (m.w[q]) atomicOr(Fn + (size_t)c * W + q, m.w[q]);
+                    if (__ldcg(a.qmark + c) != d + 1 && atomicExch(a.qmark + c, d + 1) != d + 1) {
+                        cg::coalesced_group g = cg::coalesced_threads();
+                        int pos = 0;
+                        if (g.thread_rank() == 0) pos = atomicAdd(a.qcnt + d + 1, (int)g.size());
+                        pos = g.shfl(pos, 0) + (int)g.thread_rank();
+                        if (qtail + pos < a.qcap) a.queue[qtail + pos] = c;
+                    }
+                }
+            });
+            if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+            // ---- top-down (b): every new vertex pulls sigma for its new bits
+            nq1 = __ldcg(a.qcnt + d + 1);
+            queued = qtail + nq1 <= a.qcap;
+            for_level<W>(a, queued ? (int)qtail : -1, nq1, Fn, [&](int w) {
+                const Bits<W> t = load_bits<W>(Fn + (size_t)w * W);
+                const Bits<W> vold = load_bits<W>(a.vis + (size_t)w * W);
+                unsigned long long acc[2 * W];
+                double facc[2 * W];
+#pragma unroll
+                for (int k = 0; k < 2 * W; ++k) acc[k] = 0;
+                gather<W, false>(a, __ldg(a.rp + w), __ldg(a.rp + w + 1), Fd, t, acc, facc, ovf);
+                settle<W>(a, w, vold, t, act, acc, nullptr, &bc);
+            });
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                if (bc.v) atomicAdd(a.vcnt + d + 1, bc.v);
+                if (bc.mf) atomicAdd(a.mfv + d + 1, bc.mf);
+                if (bc.dmu) atomicAdd(a.dmu + d + 1, bc.dmu);
+            }
+            if (tid == 0) a.qoff[d + 1] = queued ? (int)qtail : -1;
+            if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+        }
+        const int c = __ldcg(a.vcnt + d + 1);
+        if (use_bu) {
+            ++bu;
+            qo = -1;
+            nq = c;
+        } else {
+            ++td;
+            qo = queued ? (int)qtail : -1;
+            nq = queued ? nq1 : c;
+            if (queued) qtail += nq1;
+        }
+        mu -= (long long)__ldcg(a.dmu + d + 1);
+        mf = (long long)__ldcg(a.mfv + d + 1);
+        ++d;
+        if (c == 0) break;
+        if (d + 1 > a.lcap) {
+            if (tid == 0) atomicCAS(&a.ctrl->err, 0, kErrDepth);
+            return;
+        }
+    }
+    const int D = d - 1;
+    if (tid == 0) {
+        a.ctrl->depth = D;
+        a.ctrl->td_levels = td;
+        a.ctrl->bu_levels = bu;
+    }
+    if (ovf) atomicOr(&a.ctrl->ovf, 1);
+
+    // ---- backward sweep, deepest level first
+    for (int l = D; l >= 1; --l) {
+        const unsigned long long *Fl = a.F + (size_t)l * slab;
+        const unsigned long long *Fs = a.F + (size_t)(l + 1) * slab;
+        const int ql = __ldcg(a.qoff + l);
+        const int nl = ql >= 0 ? __ldcg(a.qcnt + l) : 0;
+        for_level<W>(a, ql, nl, Fl, [&](int v) {
+            const Bits<W> mv = load_bits<W>(Fl + (size_t)v * W);
+            unsigned long long acc[2 * W];
+            double facc[2 * W];
+#pragma unroll
+            for (int k = 0; k < 2 * W; ++k) facc[k] = 0.0;
+            bool dummy = false;
+            gather<W, true>(a, __ldg(a.rp + v), __ldg(a.rp + v + 1), Fs, mv, acc, facc, dummy);
+            double part = 0.0;
+            unsigned long long *row = a.sp + (size_t)v * B + lane;
+#pragma unroll
+            for (int k = 0; k < 2 * W; ++k) {
+                if (has_slot<W>(mv, k, lane)) {
+                    const double sv = __ull2double_rn(__ldcg(row + 32 * k));
+                    const double delta = __dmul_rn(sv, facc[k]);
+                    row[32 * k] = (unsigned long long)__double_as_longlong(__ddiv_rn(__dadd_rn(1.0, delta), sv));
+                    part += delta;
+                }
+            }
+            part = dev::group_sum<32>(part);
+            if (lane == 0 && part != 0.0) a.scores[v] += part;
+        });
+        if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+    }
+}
+
+// ------------------------------------------------------------------ host side
+template <int W> int blocks_per_sm()
+{
+    static int b = -1;
+    if (b < 0) {
+        int v = 0;
+        NK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_batch<W>, kThreads, 0));
+        b = v;
+    }
+    return b;
+}
+
+struct Layout {
+    int W, B, lcap;
+    int64_t qcap;
+    size_t off_F, off_vis, off_sp, off_qmark, off_queue, off_cnt, total;
+};
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+Layout layout(const nk_graph *g, int B, int lcap)
+{
+    Layout L;
+    L.B = B;
+    L.W = B / 64;
+    L.lcap = lcap;
+    L.qcap = 2 * (int64_t)g->n + 64;
+    const size_t n = (size_t)g->n;
+    size_t o = 0;
+    L.off_F = o;
+    o = align_up(o + (size_t)(lcap + 2) * n * L.W * 8);
+    L.off_vis = o;
+    o = align_up(o + n * L.W * 8);
+    L.off_sp = o;
+    o = align_up(o + n * (size_t)B * 8);
+    L.off_qmark = o;
+    o = align_up(o + n * 4);
+    L.off_queue = o;
+    o = align_up(o + (size_t)L.qcap * 4);
+    L.off_cnt = o;
+    o = align_up(o + (size_t)(lcap + 3) * (3 * 4 + 2 * 8));
+    L.total = o;
+    return L;
+}
+
+int choose_lcap(const nk_graph *g, int B, const DevBuf *ws)
+{
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const size_t slab = (size_t)g->n * (B / 64) * 8;
+    const Layout base = layout(g, B, 0);
+    // level slabs may use up to half of what is free after the rest of the batch state
+    const size_t have = free_b + ws[5].bytes;
+    size_t budget = have > base.total ? (have - base.total) / 2 : 0;
+    int64_t l = slab ? (int64_t)(budget / slab) - 2 : 1022;
+    l = std::min<int64_t>(l, 1022);
+    l = std::min<int64_t>(l, (int64_t)g->n);
+    return (int)std::max<int64_t>(l, 0);
+}
+
+enum { WS_BATCH = 5, WS_BCTRL = 6 };
+
+template <int W>
+int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores,
+                   const RunCfg &cfg, RunStats *st, cudaStream_t s)
+{
+    constexpr int B = 64 * W;
+    DevBuf *ws = scratch(cfg, g);
+    const int lcap = cfg.lcap > 0 ? std::min(cfg.lcap, std::max(g->n, 4)) : choose_lcap(g, B, ws);
+    if (lcap < 4) return set_error(NK_ERR_NOMEM, "not enough device memory for a batch of %d sources", B);
+    const Layout L = layout(g, B, lcap);
+    NK_TRY(ws[WS_BATCH].ensure(L.total));
+    const int nb = (k + B - 1) / B;
+    NK_TRY(ws[WS_BCTRL].ensure(sizeof(Ctrl) * nb));
+    const int bps = blocks_per_sm<W>();
+    if (bps < 1) return set_error(NK_ERR_CUDA, "batched kernel cannot be resident");
+    char *base = ws[WS_BATCH].as<char>();
+    BArgs a;
+    a.n = g->n;
+    a.A = g->A;
+    a.rp = g->rp.as<int32_t>();
+    a.col = g->col.as<int32_t>();
+    a.lcap = lcap;
+    a.F = reinterpret_cast<unsigned long long *>(base + L.off_F);
+    a.vis = reinterpret_cast<unsigned long long *>(base + L.off_vis);
+    a.sp = reinterpret_cast<unsigned long long *>(base + L.off_sp);
+    a.qmark = reinterpret_cast<int32_t *>(base + L.off_qmark);
+    a.queue = reinterpret_cast<int32_t *>(base + L.off_queue);
+    a.qcap = L.qcap;
+    const size_t lv = (size_t)lcap + 3;
+    char *cb = base + L.off_cnt;
+    a.mfv = reinterpret_cast<unsigned long long *>(cb);
+    a.dmu = a.mfv + lv;
+    a.vcnt = reinterpret_cast<int32_t *>(a.dmu + lv);
+    a.qcnt = a.vcnt + lv;
+    a.qoff = a.qcnt + lv;
+    a.scores = d_scores;
+    a.limit_ns = cfg.limit_ns ? cfg.limit_ns : wait_limit_ns();
+    a.alpha = cfg.alpha > 0 ? cfg.alpha : 1.0;
+    a.dir = cfg.direction;
+    Ctrl *ctrls = ws[WS_BCTRL].as<Ctrl>();
+    NK_CUDA(cudaMemsetAsync(ctrls, 0, sizeof(Ctrl) * nb, s));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cfg.time_kernels) {
+        NK_CUDA(cudaEventCreate(&e0));
+        NK_CUDA(cudaEventCreate(&e1));
+        NK_CUDA(cudaEventRecord(e0, s));
+    }
+    const int grid = std::max(1, bps * num_sms() / std::max(1, cfg.grid_div));
+    for (int bi = 0; bi < nb; ++bi) {
+        a.src = d_src + (size_t)bi * B;
+        a.nsrc = std::min(B, k - bi * B);
+        a.ctrl = ctrls + bi;
+        void *args[] = {&a};
+        NK_CUDA(cudaLaunchCooperativeKernel((const void *)k_batch<W>, dim3(grid), dim3(kThreads), args, 0, s));
+    }
+    if (cfg.time_kernels) NK_CUDA(cudaEventRecord(e1, s));
+    std::vector<Ctrl> h(nb);
+    NK_CUDA(cudaMemcpyAsync(h.data(), ctrls, sizeof(Ctrl) * nb, cudaMemcpyDeviceToHost, s));
+    NK_CUDA(cudaStreamSynchronize(s));
+    if (st) {
+        st->mode = NK_MODE_BATCHED;
+        st->batch = B;
+        st->tpv = 32;
+        st->launches += nb;
+        st->alpha = a.alpha;
+        for (const Ctrl &c : h) {
+            st->max_depth = std::max(st->max_depth, c.depth);
+            st->td_levels += c.td_levels;
+            st->bu_levels += c.bu_levels;
+        }
+        if (cfg.time_kernels) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            st->kernel_ms += ms;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    bool ovf = false;
+    for (int bi = 0; bi < nb; ++bi) {
+        if (h[bi].err == NK_ERR_TIMEOUT) return set_error(NK_ERR_TIMEOUT, "batched sweep aborted: a bounded grid wait ran out");
+        ovf |= h[bi].ovf != 0;
+    }
+    if (ovf) return set_error(NK_ERR_OVERFLOW, "a shortest-path count exceeded 2^64 - 1");
+    // batches deeper than the level slabs: their sources go through the per-source form
+    for (int bi = 0; bi < nb; ++bi) {
+        if (h[bi].err != kErrDepth) continue;
+        RunCfg pc = cfg;
+        pc.tpv = 0;
+        NK_TRY(run_per_source(g, d_src + (size_t)bi * B, std::min(B, k - bi * B), d_scores, pc, st, s));
+    }
+    return NK_OK;
+}
+
+}  // namespace
+
+size_t batched_bytes(const nk_graph *g, int B) { return layout(g, B, 16).total; }
+
+size_t batched_bytes_lcap(const nk_graph *g, int B, int lcap) { return layout(g, B, lcap).total; }
+
+int run_batched(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores,
+                const RunCfg &cfg, RunStats *st, cudaStream_t s)
+{
+    int B = cfg.batch;
+    if (B == 0) B = g->tuned.valid ? g->tuned.batch : 64;
+    switch (B) {
+    case 64: return launch_batches<1>(g, d_src, k, d_scores, cfg, st, s);
+    case 128: return launch_batches<2>(g, d_src, k, d_scores, cfg, st, s);
+    case 256: return launch_batches<4>(g, d_src, k, d_scores, cfg, st, s);
+    default: return set_error(NK_ERR_ARG, "batch must be 64, 128 or 256 (got %d)", B);
+    }
+}
+
+}  // namespace nk

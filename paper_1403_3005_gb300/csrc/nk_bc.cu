@@ -1,0 +1,259 @@
+// Betweenness entry points of the C ABI: argument checks, host/device staging, choice
+// between the per-source and the batched form, final scaling, the per-thread run
+// statistics and the autotuner.
+//
+// Scaling (Section 3.2): exact betweenness halves the sum of all n dependency vectors
+// (every unordered pair {s,t} is reached from both ends); the sampled estimate scales
+// the sum over k sources by n/(2k), so that its expectation is the exact value.
+#include <algorithm>
+#include <vector>
+
+#include "nk_device.cuh"
+#include "nk_internal.h"
+
+namespace nk {
+namespace {
+
+thread_local RunStats t_stats;
+
+__global__ void k_iota(int32_t *p, int32_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = (int32_t)i;
+}
+
+__global__ void k_check_src(const int32_t *src, int32_t k, int32_t n, int *bad)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if ((unsigned)src[i] >= (unsigned)n) atomicOr(bad, 1);
+}
+
+RunCfg cfg_of(const nk_run_opts *o, const nk_graph *g)
+{
+    RunCfg c;
+    if (o) {
+        c.mode = o->mode;
+        c.batch = o->batch;
+        c.tpv = o->tpv;
+        c.direction = o->direction;
+        c.alpha = o->alpha;
+        c.time_kernels = (o->flags & NK_RUN_TIME_KERNELS) != 0;
+    }
+    if (c.alpha <= 0 && g->tuned.valid) c.alpha = g->tuned.alpha;
+    return c;
+}
+
+int check_cfg(const RunCfg &c)
+{
+    if (c.mode < NK_MODE_AUTO || c.mode > NK_MODE_BATCHED) return set_error(NK_ERR_ARG, "bad mode %d", c.mode);
+    if (c.direction < NK_DIR_AUTO || c.direction > NK_DIR_BOTTOM_UP) return set_error(NK_ERR_ARG, "bad direction %d", c.direction);
+    if (c.batch != 0 && c.batch != 64 && c.batch != 128 && c.batch != 256) return set_error(NK_ERR_ARG, "batch must be 0, 64, 128 or 256");
+    if (c.tpv != 0 && (c.tpv < 1 || c.tpv > 32 || (c.tpv & (c.tpv - 1)))) return set_error(NK_ERR_ARG, "tpv must be 0 or a power of two <= 32");
+    if (!(c.alpha >= 0)) return set_error(NK_ERR_ARG, "alpha must be >= 0");
+    return NK_OK;
+}
+
+// scores (device, zeroed here) += dependencies of the k device sources, then *= scale
+int run_device(nk_graph *g, const int32_t *d_src, int32_t k, double scale, double *d_scores,
+               const RunCfg &cfg, cudaStream_t s)
+{
+    NK_CUDA(cudaMemsetAsync(d_scores, 0, sizeof(double) * g->n, s));
+    t_stats = RunStats();
+    int mode = cfg.mode;
+    if (mode == NK_MODE_AUTO) mode = k >= 16 ? NK_MODE_BATCHED : NK_MODE_PER_SOURCE;
+    int rc;
+    if (mode == NK_MODE_BATCHED) {
+        rc = run_batched(g, d_src, k, d_scores, cfg, &t_stats, s);
+        if (rc == NK_ERR_NOMEM && cfg.mode == NK_MODE_AUTO) {
+            NK_CUDA(cudaMemsetAsync(d_scores, 0, sizeof(double) * g->n, s));
+            t_stats = RunStats();
+            rc = run_per_source(g, d_src, k, d_scores, cfg, &t_stats, s);
+        }
+    } else {
+        rc = run_per_source(g, d_src, k, d_scores, cfg, &t_stats, s);
+    }
+    if (rc != NK_OK) return rc;
+    return scale_vector(d_scores, g->n, scale, s);
+}
+
+// Common path of every betweenness entry point.  src == nullptr means "all vertices";
+// sample_k > 0 means "sample_k sources from sample_seed".
+int bc_entry(const nk_graph *gc, const int32_t *src, int32_t k, bool sample, uint64_t seed,
+             double scale, double *scores, const nk_run_opts *opts)
+{
+    if (!gc) return set_error(NK_ERR_ARG, "graph is null");
+    if (!scores) return set_error(NK_ERR_ARG, "scores is null");
+    nk_graph *g = const_cast<nk_graph *>(gc);  // only the cached workspace is written
+    const int32_t n = g->n;
+    if (k < 1 || (sample && k > n)) return set_error(NK_ERR_ARG, "need 1 <= k <= n (k=%d, n=%d)", k, n);
+    RunCfg cfg = cfg_of(opts, g);
+    NK_TRY(check_cfg(cfg));
+    const bool dev = opts && (opts->flags & NK_RUN_DEVICE_PTRS);
+    cudaStream_t s = stream();
+    std::lock_guard<std::mutex> lock(g->mu);
+    Tmp dsrc, dscores, flag;
+    const int32_t *d_src = nullptr;
+    if (sample) {
+        NK_TRY(dsrc.alloc(sizeof(int32_t) * k, s));
+        NK_TRY(sample_sources_device(n, seed, k, dsrc.as<int32_t>(), s));
+        d_src = dsrc.as<int32_t>();
+    } else if (!src) {
+        NK_TRY(dsrc.alloc(sizeof(int32_t) * k, s));
+        k_iota<<<std::max(1, std::min((k + 255) / 256, 8 * num_sms())), 256, 0, s>>>(dsrc.as<int32_t>(), k);
+        NK_CUDA(cudaGetLastError());
+        d_src = dsrc.as<int32_t>();
+    } else {
+        if (dev) {
+            d_src = src;
+        } else {
+            NK_TRY(dsrc.alloc(sizeof(int32_t) * k, s));
+            NK_CUDA(cudaMemcpyAsync(dsrc.p, src, sizeof(int32_t) * k, cudaMemcpyHostToDevice, s));
+            d_src = dsrc.as<int32_t>();
+        }
+        NK_TRY(flag.alloc(sizeof(int), s));
+        NK_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
+        k_check_src<<<std::max(1, std::min((k + 255) / 256, 8 * num_sms())), 256, 0, s>>>(d_src, k, n, flag.as<int>());
+        int hb = 0;
+        NK_CUDA(cudaMemcpyAsync(&hb, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+        NK_CUDA(cudaStreamSynchronize(s));
+        if (hb) return set_error(NK_ERR_ARG, "a source id is outside [0, %d)", n);
+    }
+    double *d_scores = scores;
+    if (!dev) {
+        NK_TRY(dscores.alloc(sizeof(double) * n, s));
+        d_scores = dscores.as<double>();
+    }
+    NK_TRY(run_device(g, d_src, k, scale, d_scores, cfg, s));
+    if (!dev) NK_CUDA(cudaMemcpyAsync(scores, d_scores, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    NK_CUDA(cudaStreamSynchronize(s));
+    return NK_OK;
+}
+
+}  // namespace
+}  // namespace nk
+
+using namespace nk;
+
+extern "C" {
+
+int nk_betweenness_exact(const nk_graph *g, double *scores)
+{
+    if (!g) return set_error(NK_ERR_ARG, "graph is null");
+    return bc_entry(g, nullptr, g->n, false, 0, 0.5, scores, nullptr);
+}
+
+int nk_betweenness_sampled(const nk_graph *g, uint64_t seed, int32_t k, double *scores)
+{
+    return nk_betweenness_sampled_opts(g, seed, k, scores, nullptr);
+}
+
+int nk_betweenness_sampled_opts(const nk_graph *g, uint64_t seed, int32_t k, double *scores,
+                                const nk_run_opts *opts)
+{
+    if (!g) return set_error(NK_ERR_ARG, "graph is null");
+    if (k < 1 || k > g->n) return set_error(NK_ERR_ARG, "need 1 <= k <= n (k=%d, n=%d)", k, g->n);
+    return bc_entry(g, nullptr, k, true, seed, (double)g->n / (2.0 * (double)k), scores, opts);
+}
+
+int nk_betweenness_sources(const nk_graph *g, const int32_t *src, int32_t k, double scale,
+                           double *scores, const nk_run_opts *opts)
+{
+    if (!src) return set_error(NK_ERR_ARG, "src is null");
+    return bc_entry(g, src, k, false, 0, scale, scores, opts);
+}
+
+int nk_last_run_stats(nk_run_stats *out)
+{
+    if (!out) return set_error(NK_ERR_ARG, "out is null");
+    out->mode = t_stats.mode;
+    out->batch = t_stats.batch;
+    out->tpv = t_stats.tpv;
+    out->max_depth = t_stats.max_depth;
+    out->launches = t_stats.launches;
+    out->kernel_ms = t_stats.kernel_ms;
+    out->td_levels = t_stats.td_levels;
+    out->bu_levels = t_stats.bu_levels;
+    out->alpha = t_stats.alpha;
+    return NK_OK;
+}
+
+int nk_sssp(const nk_graph *gc, int32_t s, int32_t *dist, uint64_t *sigma)
+{
+    if (!gc || !dist || !sigma) return set_error(NK_ERR_ARG, "null argument");
+    nk_graph *g = const_cast<nk_graph *>(gc);
+    if (s < 0 || s >= g->n) return set_error(NK_ERR_ARG, "source %d outside [0, %d)", s, g->n);
+    cudaStream_t st = stream();
+    std::lock_guard<std::mutex> lock(g->mu);
+    Tmp dd, ds;
+    NK_TRY(dd.alloc(sizeof(int32_t) * g->n, st));
+    NK_TRY(ds.alloc(sizeof(uint64_t) * g->n, st));
+    const int rc = run_sssp(g, s, dd.as<int32_t>(), ds.as<uint64_t>(), st);
+    if (rc != NK_OK && rc != NK_ERR_OVERFLOW) return rc;
+    NK_CUDA(cudaMemcpyAsync(dist, dd.p, sizeof(int32_t) * g->n, cudaMemcpyDeviceToHost, st));
+    NK_CUDA(cudaMemcpyAsync(sigma, ds.p, sizeof(uint64_t) * g->n, cudaMemcpyDeviceToHost, st));
+    NK_CUDA(cudaStreamSynchronize(st));
+    return rc;
+}
+
+int nk_autotune(const nk_graph *gc, uint64_t seed, int32_t k, nk_run_opts *best)
+{
+    if (!gc || !best) return set_error(NK_ERR_ARG, "null argument");
+    nk_graph *g = const_cast<nk_graph *>(gc);
+    if (k < 1 || k > g->n) return set_error(NK_ERR_ARG, "need 1 <= k <= n");
+    cudaStream_t s = stream();
+    std::lock_guard<std::mutex> lock(g->mu);
+    // the sample: the first min(k, 256) of the run's own sources
+    const int32_t ks = std::min<int32_t>(k, 256);
+    Tmp dsrc, dsc;
+    NK_TRY(dsrc.alloc(sizeof(int32_t) * k, s));
+    NK_TRY(dsc.alloc(sizeof(double) * g->n, s));
+    NK_TRY(sample_sources_device(g->n, seed, k, dsrc.as<int32_t>(), s));
+    auto trial = [&](int B, double alpha, double *ms_per_src) -> int {
+        RunCfg c;
+        c.mode = NK_MODE_BATCHED;
+        c.batch = B;
+        c.alpha = alpha;
+        c.time_kernels = true;
+        const int32_t kk = std::min<int32_t>(ks, B);
+        NK_CUDA(cudaMemsetAsync(dsc.p, 0, sizeof(double) * g->n, s));
+        RunStats st;
+        NK_TRY(run_batched(g, dsrc.as<int32_t>(), kk, dsc.as<double>(), c, &st, s));  // warm
+        st = RunStats();
+        NK_TRY(run_batched(g, dsrc.as<int32_t>(), kk, dsc.as<double>(), c, &st, s));
+        *ms_per_src = st.kernel_ms / kk;
+        return NK_OK;
+    };
+    int bestB = 64;
+    double bestA = 1.0, bestT = 1e30;
+    for (int B : {64, 128, 256}) {
+        if (B > 64 && ks < B / 2) break;
+        double t;
+        const int rc = trial(B, 1.0, &t);
+        if (rc == NK_ERR_NOMEM) break;
+        NK_TRY(rc);
+        if (t < bestT) {
+            bestT = t;
+            bestB = B;
+        }
+    }
+    for (double alpha : {0.25, 4.0, 16.0}) {
+        double t;
+        NK_TRY(trial(bestB, alpha, &t));
+        if (t < bestT) {
+            bestT = t;
+            bestA = alpha;
+        }
+    }
+    g->tuned.valid = true;
+    g->tuned.batch = bestB;
+    g->tuned.alpha = bestA;
+    *best = nk_run_opts();
+    best->mode = NK_MODE_BATCHED;
+    best->batch = bestB;
+    best->alpha = bestA;
+    return NK_OK;
+}
+
+}  // extern "C"

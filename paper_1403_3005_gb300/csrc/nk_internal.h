@@ -1,0 +1,164 @@
+// Host-side internals of libnk: error state, stream, device buffers, graph object,
+// and the declarations shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdarg>
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include "nk.h"
+
+namespace nk {
+
+// ---------------------------------------------------------------- errors
+int set_error(int code, const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define NK_CUDA(call)                                                                 \
+    do {                                                                              \
+        cudaError_t nk_e_ = (call);                                                   \
+        if (nk_e_ != cudaSuccess) return ::nk::cuda_fail(nk_e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define NK_TRY(expr)                    \
+    do {                                \
+        int nk_rc_ = (expr);            \
+        if (nk_rc_ != NK_OK) return nk_rc_; \
+    } while (0)
+
+// ---------------------------------------------------------------- stream / limits
+cudaStream_t stream();
+uint64_t wait_limit_ns();
+int num_sms();
+
+// ---------------------------------------------------------------- device buffers
+// A growable device allocation; contents are not preserved on growth.  With a stream
+// set (`st`), allocation and release are stream-ordered (cudaMallocAsync /
+// cudaFreeAsync), which never synchronises the device; otherwise cudaMalloc.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaStream_t st = nullptr;
+    bool stream_ordered = false;
+    int ensure(size_t b);
+    void release();
+    template <class T> T *as() const { return static_cast<T *>(p); }
+    ~DevBuf() { release(); }
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+};
+
+// Stream-ordered temporary (cudaMallocAsync / cudaFreeAsync on the library stream).
+struct Tmp {
+    void *p = nullptr;
+    cudaStream_t st = nullptr;
+    int alloc(size_t b, cudaStream_t s);
+    template <class T> T *as() const { return static_cast<T *>(p); }
+    ~Tmp();
+};
+
+// ---------------------------------------------------------------- control block
+// Device-resident control words of one persistent launch (grid barrier, status).
+struct Ctrl {
+    unsigned bar_count;
+    unsigned bar_gen;
+    int err;     // NK_ERR_TIMEOUT / internal abort code; 0 while running
+    int ovf;     // sigma overflow seen
+    int depth;   // deepest BFS level
+    int td_levels;
+    int bu_levels;
+    int pad;
+};
+
+// Tuned settings remembered per graph by the autotuner.
+struct Tuned {
+    bool valid = false;
+    int batch = 64;
+    double alpha = 1.0;
+    int tpv = 8;
+};
+
+}  // namespace nk
+
+// The opaque graph handle of the C ABI.
+struct nk_graph {
+    int32_t n = 0;
+    int64_t A = 0;
+    int32_t max_deg = 0;
+    nk::DevBuf rp;   // int32[n+1]
+    nk::DevBuf col;  // int32[A] (at least 4 bytes)
+    // cached per-graph scratch of the betweenness kernels; guarded by mu
+    std::mutex mu;
+    nk::DevBuf ws[8];
+    nk::Tuned tuned;
+    std::atomic<int64_t> pending{0};  // serving requests referencing this graph
+};
+
+namespace nk {
+
+// ---------------------------------------------------------------- primitives (nk_core.cu)
+// Exclusive prefix sum of count int64 values (in may equal out); *total (device, may be
+// null) receives the sum.  Stream-ordered on st.
+int scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t count, int64_t *total,
+                       cudaStream_t st);
+
+// ---------------------------------------------------------------- CSR build (nk_graph.cu)
+// Canonical CSR of the undirected edge list (u[i], v[i]) (device arrays), written into
+// g->rp / g->col.  Returns NK_ERR_GRAPH for out-of-range ids.
+int build_csr_from_edges(nk_graph *g, int32_t n, int64_t m, const int32_t *d_u,
+                         const int32_t *d_v, cudaStream_t st);
+
+// ---------------------------------------------------------------- sampler (nk_sample.cu)
+int sample_sources_device(int32_t n, uint64_t seed, int32_t k, int32_t *d_src, cudaStream_t st);
+
+// ---------------------------------------------------------------- sweeps
+struct RunCfg {
+    int mode = NK_MODE_AUTO;
+    int batch = 0;
+    int tpv = 0;
+    int direction = NK_DIR_AUTO;
+    double alpha = 0.0;
+    bool time_kernels = false;
+    DevBuf *ws = nullptr;  // scratch slots (8); null = the graph's cached workspace
+    int grid_div = 1;      // persistent grids use 1/grid_div of the co-resident CTAs
+    int lcap = 0;          // batched level slabs; 0 = sized from free memory
+    uint64_t limit_ns = 0; // bound on device-side waits; 0 = the process-wide bound
+};
+
+inline DevBuf *scratch(const RunCfg &c, nk_graph *g);
+
+struct RunStats {
+    int mode = 0, batch = 0, tpv = 0, max_depth = 0;
+    int64_t launches = 0, td_levels = 0, bu_levels = 0;
+    double kernel_ms = 0.0, alpha = 0.0;
+};
+
+// Per-source form (nk_source.cu).  scores (device) += scale-free dependencies of each
+// source in d_src[0..k); the caller scales.  sssp mode: k = 1, scores = null, and
+// d_dist/d_sigma receive the forward sweep.
+int run_per_source(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores,
+                   const RunCfg &cfg, RunStats *st, cudaStream_t s);
+int run_sssp(nk_graph *g, int32_t src, int32_t *d_dist, uint64_t *d_sigma, cudaStream_t s);
+
+// Batched multi-source form (nk_batch.cu).  Returns NK_OK, or an error; sources of a
+// batch whose BFS is deeper than the level cap are re-run by the per-source form.
+int run_batched(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores,
+                const RunCfg &cfg, RunStats *st, cudaStream_t s);
+
+// Device bytes the batched form needs for one batch of B sources on this graph.
+size_t batched_bytes(const nk_graph *g, int B);
+
+inline DevBuf *scratch(const RunCfg &c, nk_graph *g) { return c.ws ? c.ws : g->ws; }
+
+// Device bytes of a batched run with B sources per batch and lcap level slabs.
+size_t batched_bytes_lcap(const nk_graph *g, int B, int lcap);
+
+// Scale a device vector in place.
+int scale_vector(double *d, int32_t n, double scale, cudaStream_t s);
+
+}  // namespace nk

@@ -1,0 +1,312 @@
+// Serving runtime: continuous batching of sampled-betweenness requests.
+//
+// Requests (graph, seed, k) arrive at any time and wait in a FIFO.  A request is
+// admitted as soon as one of `max_inflight` slots is free AND its device-state bytes
+// fit in what is left of the memory budget; requests that arrive while others run are
+// admitted the moment a slot and memory free up.  Each slot is a worker thread with its
+// own non-blocking CUDA stream; its request's state (sampled sources, per-batch bitset
+// levels, sigma/psi rows, scores) is allocated stream-ordered on that stream and freed
+// when the request ends, so the work of different requests - on different graphs or on
+// the same one - overlaps on the device.  The persistent kernels of a slot use
+// 1/max_inflight of the co-resident CTAs, so that up to max_inflight of them are
+// resident together.  CSR arrays stay resident in the graph objects the caller owns.
+//
+// Latency is measured from submit to the moment the scores are in the caller's buffer.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "nk_device.cuh"
+#include "nk_internal.h"
+
+namespace nk {
+namespace {
+
+using clk = std::chrono::steady_clock;
+
+struct Request {
+    nk_req id = 0;
+    nk_graph *g = nullptr;
+    uint64_t seed = 0;
+    int32_t k = 0;
+    double *scores = nullptr;
+    size_t need = 0;
+    clk::time_point t_submit, t_done;
+    int state = 0;  // 0 queued, 1 running, 2 done
+    int rc = NK_OK;
+    std::string err;
+};
+
+constexpr int kServeLcap = 64;
+
+}  // namespace
+}  // namespace nk
+
+struct nk_server {
+    nk_server_opts opts{};
+    size_t budget = 0, used = 0, peak_bytes = 0;
+    int batch = 64, slots = 8;
+    uint64_t limit_ns = 0;
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<nk::Request *> queue;
+    std::unordered_map<nk_req, nk::Request *> reqs;
+    std::vector<std::thread> workers;
+    bool draining = false, stop = false;
+    nk_req next_id = 1;
+    int64_t submitted = 0, completed = 0, failed = 0, rejected = 0;
+    int running = 0;
+    int64_t peak_inflight = 0;
+    double busy_s = 0, exs = 0;
+    nk::clk::time_point busy_since;
+    std::vector<double> lat_ms;
+};
+
+namespace nk {
+namespace {
+
+size_t request_bytes(const nk_graph *g, int B, int32_t k)
+{
+    const int lcap = std::min(kServeLcap, std::max(g->n, 4));
+    return batched_bytes_lcap(g, B, lcap) + sizeof(Ctrl) * ((size_t)(k + B - 1) / B + 1) +
+           sizeof(int32_t) * (size_t)k + sizeof(double) * (size_t)g->n + 4096;
+}
+
+int run_request(nk_server *S, Request *r, cudaStream_t st, double **h_buf, size_t *h_cap)
+{
+    nk_graph *g = r->g;
+    const int32_t n = g->n;
+    DevBuf ws[8];
+    for (auto &b : ws) {
+        b.stream_ordered = true;
+        b.st = st;
+    }
+    Tmp dsrc, dsc;
+    NK_TRY(dsrc.alloc(sizeof(int32_t) * r->k, st));
+    NK_TRY(dsc.alloc(sizeof(double) * n, st));
+    NK_TRY(sample_sources_device(n, r->seed, r->k, dsrc.as<int32_t>(), st));
+    NK_CUDA(cudaMemsetAsync(dsc.p, 0, sizeof(double) * n, st));
+    RunCfg cfg;
+    cfg.mode = NK_MODE_BATCHED;
+    cfg.batch = S->batch;
+    cfg.ws = ws;
+    cfg.grid_div = S->slots;
+    cfg.lcap = std::min(kServeLcap, std::max(n, 4));
+    cfg.limit_ns = S->limit_ns;
+    NK_TRY(run_batched(g, dsrc.as<int32_t>(), r->k, dsc.as<double>(), cfg, nullptr, st));
+    NK_TRY(scale_vector(dsc.as<double>(), n, (double)n / (2.0 * (double)r->k), st));
+    if (*h_cap < (size_t)n) {
+        if (*h_buf) cudaFreeHost(*h_buf);
+        *h_buf = nullptr;
+        *h_cap = 0;
+        NK_CUDA(cudaMallocHost(h_buf, sizeof(double) * n));
+        *h_cap = n;
+    }
+    NK_CUDA(cudaMemcpyAsync(*h_buf, dsc.p, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    NK_CUDA(cudaStreamSynchronize(st));
+    std::copy(*h_buf, *h_buf + n, r->scores);
+    return NK_OK;
+}
+
+void worker(nk_server *S)
+{
+    cudaSetDevice(S->device);
+    cudaStream_t st = nullptr;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    double *h_buf = nullptr;
+    size_t h_cap = 0;
+    for (;;) {
+        Request *r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_work.wait(lk, [&] {
+                return S->stop || (!S->queue.empty() && S->used + S->queue.front()->need <= S->budget);
+            });
+            if (S->stop) break;
+            r = S->queue.front();
+            S->queue.pop_front();
+            S->used += r->need;
+            S->peak_bytes = std::max(S->peak_bytes, S->used);
+            if (S->running++ == 0) S->busy_since = clk::now();
+            S->peak_inflight = std::max<int64_t>(S->peak_inflight, S->running);
+            r->state = 1;
+        }
+        const int rc = run_request(S, r, st, &h_buf, &h_cap);
+        const std::string msg = rc == NK_OK ? std::string() : std::string(nk_last_error());
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            r->t_done = clk::now();
+            r->rc = rc;
+            r->err = msg;
+            r->state = 2;
+            S->used -= r->need;
+            if (--S->running == 0)
+                S->busy_s += std::chrono::duration<double>(r->t_done - S->busy_since).count();
+            if (rc == NK_OK) {
+                ++S->completed;
+                S->lat_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+                S->exs += (double)(r->g->A / 2) * (double)r->k;
+            } else {
+                ++S->failed;
+            }
+            r->g->pending.fetch_sub(1);
+        }
+        S->cv_done.notify_all();
+        S->cv_work.notify_all();
+    }
+    if (h_buf) cudaFreeHost(h_buf);
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+}
+
+double pct(std::vector<double> v, double p)
+{
+    if (v.empty()) return 0.0;
+    std::sort(v.begin(), v.end());
+    // nearest-rank percentile
+    size_t idx = (size_t)std::ceil(p / 100.0 * (double)v.size());
+    idx = std::min(std::max<size_t>(idx, 1), v.size());
+    return v[idx - 1];
+}
+
+}  // namespace
+}  // namespace nk
+
+using namespace nk;
+
+extern "C" {
+
+int nk_server_create(const nk_server_opts *opts, nk_server **out)
+{
+    if (!out) return set_error(NK_ERR_ARG, "out is null");
+    *out = nullptr;
+    nk_server_opts o{};
+    if (opts) o = *opts;
+    if (o.batch != 0 && o.batch != 64 && o.batch != 128 && o.batch != 256)
+        return set_error(NK_ERR_ARG, "batch must be 0, 64, 128 or 256");
+    if (o.max_inflight < 0 || o.max_inflight > 64) return set_error(NK_ERR_ARG, "max_inflight must be in [0, 64]");
+    if (!(o.mem_budget_bytes >= 0) || !(o.timeout_s >= 0)) return set_error(NK_ERR_ARG, "negative budget or timeout");
+    nk_server *S = new (std::nothrow) nk_server();
+    if (!S) return set_error(NK_ERR_NOMEM, "host allocation failed");
+    S->opts = o;
+    NK_CUDA(cudaGetDevice(&S->device));
+    size_t free_b = 0, total_b = 0;
+    NK_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    S->budget = o.mem_budget_bytes > 0 ? (size_t)o.mem_budget_bytes : (size_t)(0.6 * (double)free_b);
+    S->slots = o.max_inflight > 0 ? o.max_inflight : 8;
+    S->batch = o.batch > 0 ? o.batch : 64;
+    S->limit_ns = o.timeout_s > 0 ? (uint64_t)(o.timeout_s * 1e9) : 0;
+    for (int i = 0; i < S->slots; ++i) S->workers.emplace_back(worker, S);
+    *out = S;
+    return NK_OK;
+}
+
+void nk_server_destroy(nk_server *S)
+{
+    if (!S) return;
+    {
+        std::unique_lock<std::mutex> lk(S->mu);
+        S->draining = true;
+        S->cv_done.wait(lk, [&] { return S->queue.empty() && S->running == 0; });
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    for (auto &t : S->workers) t.join();
+    for (auto &kv : S->reqs) delete kv.second;
+    delete S;
+}
+
+int nk_serve_submit(nk_server *S, const nk_graph *gc, uint64_t seed, int32_t k, double *scores,
+                    nk_req *id)
+{
+    if (!S || !gc || !scores || !id) return set_error(NK_ERR_ARG, "null argument");
+    nk_graph *g = const_cast<nk_graph *>(gc);
+    if (k < 1 || k > g->n) return set_error(NK_ERR_ARG, "need 1 <= k <= n (k=%d, n=%d)", k, g->n);
+    Request *r = new (std::nothrow) Request();
+    if (!r) return set_error(NK_ERR_NOMEM, "host allocation failed");
+    r->g = g;
+    r->seed = seed;
+    r->k = k;
+    r->scores = scores;
+    r->need = request_bytes(g, S->batch, k);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->draining) {
+            delete r;
+            return set_error(NK_ERR_SHUTDOWN, "server is shutting down");
+        }
+        if (r->need > S->budget) {
+            ++S->rejected;
+            const size_t need = r->need;
+            delete r;
+            return set_error(NK_ERR_NOMEM, "request needs %zu device bytes, budget is %zu", need, S->budget);
+        }
+        r->id = S->next_id++;
+        r->t_submit = clk::now();
+        g->pending.fetch_add(1);
+        S->queue.push_back(r);
+        S->reqs[r->id] = r;
+        ++S->submitted;
+        *id = r->id;
+    }
+    S->cv_work.notify_one();
+    return NK_OK;
+}
+
+int nk_serve_poll(nk_server *S, nk_req id)
+{
+    if (!S) return set_error(NK_ERR_ARG, "server is null");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(id);
+    if (it == S->reqs.end()) return set_error(NK_ERR_ARG, "unknown request %lld", (long long)id);
+    Request *r = it->second;
+    if (r->state != 2) return NK_PENDING;
+    const int rc = r->rc;
+    if (rc != NK_OK) set_error(rc, "%s", r->err.c_str());
+    S->reqs.erase(it);
+    delete r;
+    return rc;
+}
+
+int nk_serve_wait(nk_server *S, nk_req id, double timeout_s)
+{
+    if (!S) return set_error(NK_ERR_ARG, "server is null");
+    {
+        std::unique_lock<std::mutex> lk(S->mu);
+        auto it = S->reqs.find(id);
+        if (it == S->reqs.end()) return set_error(NK_ERR_ARG, "unknown request %lld", (long long)id);
+        Request *r = it->second;
+        const auto dl = clk::now() + std::chrono::duration_cast<clk::duration>(std::chrono::duration<double>(timeout_s));
+        if (!S->cv_done.wait_until(lk, dl, [&] { return r->state == 2; })) return NK_PENDING;
+    }
+    return nk_serve_poll(S, id);
+}
+
+int nk_server_get_stats(nk_server *S, nk_server_stats *out)
+{
+    if (!S || !out) return set_error(NK_ERR_ARG, "null argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    out->submitted = S->submitted;
+    out->completed = S->completed;
+    out->failed = S->failed;
+    out->rejected = S->rejected;
+    out->p50_ms = pct(S->lat_ms, 50);
+    out->p99_ms = pct(S->lat_ms, 99);
+    out->max_ms = S->lat_ms.empty() ? 0.0 : *std::max_element(S->lat_ms.begin(), S->lat_ms.end());
+    double busy = S->busy_s;
+    if (S->running > 0) busy += std::chrono::duration<double>(clk::now() - S->busy_since).count();
+    out->busy_s = busy;
+    out->edges_x_sources = S->exs;
+    out->peak_inflight = S->peak_inflight;
+    out->peak_bytes = (double)S->peak_bytes;
+    return NK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,397 @@
+// Per-source betweenness sweep: the plain GPU form of Brandes' algorithm (Section 3.2,
+// Table 1), one shortest-path tree at a time.  It is the baseline the batched form is
+// measured against, and the fallback for very deep BFS trees.
+//
+// One cooperative (co-resident) launch per source runs every level of that source:
+//   init      dist = -1, sigma = 0; dist[s] = 0, sigma[s] = 1
+//   forward   level-synchronous BFS (Section 3.4: BFS for unweighted graphs); per level
+//             either
+//             - top-down: groups of TPV lanes expand the frontier vertices; atomicCAS on
+//               dist claims a vertex for level d+1 and appends it to the queue
+//               (warp-aggregated), and every arc (v,w) with dist[w] = d+1 adds sigma[v]
+//               to sigma[w] (atomicAdd; a carry out of 64 bits is flagged), or
+//             - bottom-up: every unvisited w sums sigma[v] over ALL neighbours v at
+//               level d (no early exit: sigma needs every parent) and joins level d+1 if
+//               the sum is non-zero; levels found this way are not queued and are later
+//               iterated by scanning dist;
+//             bottom-up is chosen when alpha * (arcs of the frontier) > (arcs of the
+//             unvisited vertices).
+//   backward  deepest level first, every v at level d pulls from its successors:
+//               acc = sum_{w in N(v), dist w = d+1} psi[w],  psi = (1 + delta) / sigma,
+//               delta_s(v) = sigma[v] * acc,  scores[v] += delta_s(v),
+//             which is Brandes' recurrence delta(v) = sum sigma_v/sigma_w (1 + delta_w)
+//             with the common factor sigma_v taken out.  psi overwrites sigma in place
+//             once a vertex's level is done (sigma of level d is still intact while
+//             level d reads psi of level d+1).
+// The levels are separated by a bounded grid barrier; per-level counters live in
+// arrays indexed by level, so every CTA reads the same values after a barrier.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "nk_device.cuh"
+#include "nk_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace nk {
+namespace {
+
+constexpr int kThreads = 512;
+
+struct SrcArgs {
+    int32_t n;
+    int64_t A;
+    const int32_t *rp, *col;
+    const int32_t *src;  // the source is *src
+    int32_t *dist;
+    unsigned long long *sp;  // sigma during the forward sweep, then psi (double bits)
+    int32_t *queue;
+    int32_t *cnt;        // cnt[d]: vertices at level d
+    long long *mfa;      // mfa[d]: sum of the degrees of level d
+    int32_t *qoff;       // qoff[d]: start of level d in queue, -1 if level d is not queued
+    double *scores;      // += delta_s (not touched when forward_only)
+    Ctrl *ctrl;
+    uint64_t limit_ns;
+    double alpha;
+    int dir;
+    int forward_only;
+};
+
+template <int TPV> struct Lanes {
+    int lane, lg, gw;
+    long long wid, nw;
+    __device__ Lanes()
+    {
+        lane = threadIdx.x & 31;
+        lg = lane % TPV;
+        gw = lane / TPV;
+        wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    }
+};
+
+__device__ __forceinline__ int degree(const int32_t *rp, int v) { return __ldg(rp + v + 1) - __ldg(rp + v); }
+
+// ------------------------------------------------------------------ top-down level d
+template <int TPV>
+__device__ void td_level(const SrcArgs &a, int d, int qo, int nf, int qnext,
+                         unsigned long long *s_mf, bool &ovf)
+{
+    constexpr int G = 32 / TPV;
+    const Lanes<TPV> L;
+    const long long count = qo >= 0 ? nf : a.n;
+    for (long long base = L.wid * G; base < count; base += L.nw * G) {
+        const long long item = base + L.gw;
+        int v = -1;
+        if (item < count) {
+            if (qo >= 0) v = dev::ldcg(a.queue + qo + item);
+            else if (dev::ldcg(a.dist + item) == d) v = (int)item;
+        }
+        if (v < 0) continue;
+        const unsigned long long sv = dev::ldcg(a.sp + v);
+        const int beg = __ldg(a.rp + v), end = __ldg(a.rp + v + 1);
+        for (int j = beg + L.lg; j < end; j += TPV) {
+            const int w = __ldg(a.col + j);
+            int dw = dev::ldcg(a.dist + w);
+            bool claim = false;
+            if (dw < 0) {
+                const int old = atomicCAS(a.dist + w, -1, d + 1);
+                claim = old < 0;
+                dw = claim ? d + 1 : old;
+            }
+            if (dw == d + 1) {
+                const unsigned long long old = atomicAdd(a.sp + w, sv);
+                ovf |= old + sv < old;
+            }
+            if (claim) {
+                cg::coalesced_group g = cg::coalesced_threads();
+                int pos = 0;
+                if (g.thread_rank() == 0) pos = atomicAdd(a.cnt + d + 1, (int)g.size());
+                pos = g.shfl(pos, 0) + (int)g.thread_rank();
+                a.queue[qnext + pos] = w;
+                atomicAdd(s_mf, (unsigned long long)degree(a.rp, w));
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ bottom-up level d
+template <int TPV>
+__device__ void bu_level(const SrcArgs &a, int d, int *s_cnt, unsigned long long *s_mf, bool &ovf)
+{
+    constexpr int G = 32 / TPV;
+    const Lanes<TPV> L;
+    for (long long base = L.wid * G; base < a.n; base += L.nw * G) {
+        const long long w = base + L.gw;
+        const bool act = w < a.n && dev::ldcg(a.dist + w) < 0;
+        unsigned long long acc = 0;
+        int beg = 0, end = 0;
+        if (act) {
+            beg = __ldg(a.rp + w);
+            end = __ldg(a.rp + w + 1);
+            for (int j = beg + L.lg; j < end; j += TPV) {
+                const int v = __ldg(a.col + j);
+                if (dev::ldcg(a.dist + v) == d) {
+                    const unsigned long long x = dev::ldcg(a.sp + v);
+                    const unsigned long long y = acc + x;
+                    ovf |= y < acc;
+                    acc = y;
+                }
+            }
+        }
+        acc = dev::group_sum_u64<TPV>(acc, ovf);
+        if (act && L.lg == 0 && acc != 0) {
+            a.dist[w] = d + 1;
+            a.sp[w] = acc;
+            atomicAdd(s_cnt, 1);
+            atomicAdd(s_mf, (unsigned long long)(end - beg));
+        }
+    }
+}
+
+// ------------------------------------------------------------------ backward level d
+template <int TPV>
+__device__ void back_level(const SrcArgs &a, int d, int qo, int nd)
+{
+    constexpr int G = 32 / TPV;
+    const Lanes<TPV> L;
+    const long long count = qo >= 0 ? nd : a.n;
+    for (long long base = L.wid * G; base < count; base += L.nw * G) {
+        const long long item = base + L.gw;
+        int v = -1;
+        if (item < count) {
+            if (qo >= 0) v = dev::ldcg(a.queue + qo + item);
+            else if (dev::ldcg(a.dist + item) == d) v = (int)item;
+        }
+        double acc = 0.0;
+        if (v >= 0) {
+            const int beg = __ldg(a.rp + v), end = __ldg(a.rp + v + 1);
+            for (int j = beg + L.lg; j < end; j += TPV) {
+                const int w = __ldg(a.col + j);
+                if (dev::ldcg(a.dist + w) == d + 1) acc += __longlong_as_double((long long)dev::ldcg(a.sp + w));
+            }
+        }
+        acc = dev::group_sum<TPV>(acc);
+        if (v >= 0 && L.lg == 0) {
+            const double sv = __ull2double_rn(dev::ldcg(a.sp + v));
+            const double delta = __dmul_rn(sv, acc);
+            a.sp[v] = (unsigned long long)__double_as_longlong(__ddiv_rn(__dadd_rn(1.0, delta), sv));
+            if (delta != 0.0) a.scores[v] += delta;
+        }
+    }
+}
+
+template <int TPV>
+__global__ void __launch_bounds__(kThreads) k_source(SrcArgs a)
+{
+    __shared__ int s_cnt;
+    __shared__ unsigned long long s_mf;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    const int s = __ldg(a.src);
+    bool ovf = false;
+    for (long long v = tid; v < a.n; v += nthr) {
+        a.dist[v] = v == s ? 0 : -1;
+        a.sp[v] = v == s ? 1ull : 0ull;
+    }
+    if (tid == 0) {
+        a.queue[0] = s;
+        a.cnt[0] = 1;
+        a.cnt[1] = 0;
+        a.mfa[1] = 0;
+        a.qoff[0] = 0;
+    }
+    if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+    const int deg_s = degree(a.rp, s);
+    long long mu = a.A - deg_s, mf = deg_s;
+    int d = 0, qo = 0, nf = 1, qtail = 1, td = 0, bu = 0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_cnt = 0;
+            s_mf = 0;
+        }
+        if (tid == 0) {
+            a.cnt[d + 2] = 0;  // used by level d+1
+            a.mfa[d + 2] = 0;
+        }
+        __syncthreads();
+        const bool use_bu = a.dir == NK_DIR_BOTTOM_UP ||
+                            (a.dir == NK_DIR_AUTO && a.alpha * (double)mf > (double)mu);
+        if (use_bu) bu_level<TPV>(a, d, &s_cnt, &s_mf, ovf);
+        else td_level<TPV>(a, d, qo, nf, qtail, &s_mf, ovf);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (s_cnt) atomicAdd(a.cnt + d + 1, s_cnt);
+            if (s_mf) atomicAdd((unsigned long long *)(a.mfa + d + 1), (unsigned long long)s_mf);
+        }
+        if (tid == 0) a.qoff[d + 1] = use_bu ? -1 : qtail;
+        if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+        const int c = dev::ldcg(a.cnt + d + 1);
+        const long long m2 = dev::ldcg(a.mfa + d + 1);
+        if (use_bu) {
+            ++bu;
+            qo = -1;
+        } else {
+            ++td;
+            qo = qtail;
+            qtail += c;
+        }
+        nf = c;
+        mu -= m2;
+        mf = m2;
+        ++d;
+        if (c == 0) break;
+    }
+    const int D = d - 1;  // deepest non-empty level
+    if (tid == 0) {
+        atomicMax(&a.ctrl->depth, D);
+        atomicAdd(&a.ctrl->td_levels, td);
+        atomicAdd(&a.ctrl->bu_levels, bu);
+    }
+    if (ovf) atomicOr(&a.ctrl->ovf, 1);
+    if (a.forward_only) return;
+    for (int l = D; l >= 1; --l) {
+        back_level<TPV>(a, l, dev::ldcg(a.qoff + l), dev::ldcg(a.cnt + l));
+        if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+    }
+}
+
+// ------------------------------------------------------------------ host side
+struct Launch {
+    const void *fn;
+    int grid;
+    int tpv;
+};
+
+template <int TPV> int make_launch(Launch &L)
+{
+    static int blocks_per_sm = -1;
+    if (blocks_per_sm < 0) {
+        int b = 0;
+        NK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_source<TPV>, kThreads, 0));
+        blocks_per_sm = b;
+    }
+    if (blocks_per_sm < 1) return set_error(NK_ERR_CUDA, "per-source kernel cannot be resident");
+    L.fn = (const void *)k_source<TPV>;
+    L.grid = blocks_per_sm * num_sms();
+    L.tpv = TPV;
+    return NK_OK;
+}
+
+int pick_launch(int tpv, Launch &L)
+{
+    switch (tpv) {
+    case 1: return make_launch<1>(L);
+    case 2: return make_launch<2>(L);
+    case 4: return make_launch<4>(L);
+    case 8: return make_launch<8>(L);
+    case 16: return make_launch<16>(L);
+    case 32: return make_launch<32>(L);
+    default: return set_error(NK_ERR_ARG, "threads per vertex must be 1, 2, 4, 8, 16 or 32 (got %d)", tpv);
+    }
+}
+
+int auto_tpv(const nk_graph *g)
+{
+    const double avg = g->n > 0 ? (double)g->A / g->n : 0.0;
+    if (avg <= 3) return 2;
+    if (avg <= 12) return 4;
+    if (avg <= 48) return 8;
+    if (avg <= 160) return 16;
+    return 32;
+}
+
+// workspace slots in nk_graph::ws used by this form
+enum { WS_DIST = 0, WS_SP = 1, WS_QUEUE = 2, WS_LEVELS = 3, WS_CTRL = 4 };
+
+int run(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores, const RunCfg &cfg,
+        RunStats *st, cudaStream_t s, bool forward_only, int32_t *d_dist_out,
+        uint64_t *d_sigma_out)
+{
+    const int32_t n = g->n;
+    DevBuf *ws = scratch(cfg, g);
+    NK_TRY(ws[WS_DIST].ensure(sizeof(int32_t) * n));
+    NK_TRY(ws[WS_SP].ensure(sizeof(uint64_t) * n));
+    NK_TRY(ws[WS_QUEUE].ensure(sizeof(int32_t) * n));
+    const size_t lv = (size_t)n + 3;
+    NK_TRY(ws[WS_LEVELS].ensure(lv * (sizeof(int32_t) * 2 + sizeof(long long))));
+    NK_TRY(ws[WS_CTRL].ensure(sizeof(Ctrl)));
+    const int tpv = cfg.tpv > 0 ? cfg.tpv : auto_tpv(g);
+    Launch L;
+    NK_TRY(pick_launch(tpv, L));
+    SrcArgs a;
+    a.n = n;
+    a.A = g->A;
+    a.rp = g->rp.as<int32_t>();
+    a.col = g->col.as<int32_t>();
+    a.dist = d_dist_out ? d_dist_out : ws[WS_DIST].as<int32_t>();
+    a.sp = d_sigma_out ? reinterpret_cast<unsigned long long *>(d_sigma_out)
+                       : ws[WS_SP].as<unsigned long long>();
+    a.queue = ws[WS_QUEUE].as<int32_t>();
+    char *lvb = ws[WS_LEVELS].as<char>();
+    a.mfa = reinterpret_cast<long long *>(lvb);
+    a.cnt = reinterpret_cast<int32_t *>(lvb + lv * sizeof(long long));
+    a.qoff = a.cnt + lv;
+    a.scores = d_scores;
+    a.ctrl = ws[WS_CTRL].as<Ctrl>();
+    a.limit_ns = cfg.limit_ns ? cfg.limit_ns : wait_limit_ns();
+    a.alpha = cfg.alpha > 0 ? cfg.alpha : 1.0;
+    a.dir = cfg.direction;
+    a.forward_only = forward_only ? 1 : 0;
+    NK_CUDA(cudaMemsetAsync(a.ctrl, 0, sizeof(Ctrl), s));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cfg.time_kernels) {
+        NK_CUDA(cudaEventCreate(&e0));
+        NK_CUDA(cudaEventCreate(&e1));
+        NK_CUDA(cudaEventRecord(e0, s));
+    }
+    for (int32_t i = 0; i < k; ++i) {
+        a.src = d_src + i;
+        void *args[] = {&a};
+        NK_CUDA(cudaLaunchCooperativeKernel(L.fn, dim3(std::max(1, L.grid / std::max(1, cfg.grid_div))), dim3(kThreads), args, 0, s));
+    }
+    if (cfg.time_kernels) NK_CUDA(cudaEventRecord(e1, s));
+    Ctrl h;
+    NK_CUDA(cudaMemcpyAsync(&h, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    NK_CUDA(cudaStreamSynchronize(s));
+    if (st) {
+        st->mode = NK_MODE_PER_SOURCE;
+        st->batch = 1;
+        st->tpv = tpv;
+        st->max_depth = std::max(st->max_depth, h.depth);
+        st->launches += k;
+        st->td_levels += h.td_levels;
+        st->bu_levels += h.bu_levels;
+        st->alpha = a.alpha;
+        if (cfg.time_kernels) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            st->kernel_ms += ms;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (h.err) return set_error(h.err, "per-source sweep aborted: a bounded grid wait ran out");
+    if (h.ovf) return set_error(NK_ERR_OVERFLOW, "a shortest-path count exceeded 2^64 - 1");
+    return NK_OK;
+}
+
+}  // namespace
+
+int run_per_source(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores,
+                   const RunCfg &cfg, RunStats *st, cudaStream_t s)
+{
+    return run(g, d_src, k, d_scores, cfg, st, s, false, nullptr, nullptr);
+}
+
+int run_sssp(nk_graph *g, int32_t src, int32_t *d_dist, uint64_t *d_sigma, cudaStream_t s)
+{
+    Tmp ds;
+    NK_TRY(ds.alloc(sizeof(int32_t), s));
+    NK_CUDA(cudaMemcpyAsync(ds.p, &src, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    RunCfg cfg;
+    return run(g, ds.as<int32_t>(), 1, nullptr, cfg, nullptr, s, true, d_dist, d_sigma);
+}
+
+}  // namespace nk

@@ -1,0 +1,274 @@
+"""GPU parity: every step of the CUDA path against the CPU oracle on the same seeded
+inputs (through the C ABI).
+
+Bars: distances, path counts, CSR arrays and sampled source sets bit-exact; FP64
+scores within 1e-9 relative with a 1e-12 absolute floor.  Every input comes from
+tests/graphs.py or from each side's own generator; the oracle never sees a GPU output.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import graphs as G
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+RTOL, ATOL = 1e-9, 1e-12
+
+
+@pytest.fixture(scope="module")
+def nk():
+    import torch
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+    from paper_1403_3005_gb300 import nk as _nk
+    _nk.lib()
+    return _nk
+
+
+def both(nk, graph):
+    """(gpu graph built from the edge list by the GPU CSR builder, oracle CSR)."""
+    n, u, v = graph
+    g = nk.graph_from_edges(n, u, v)
+    rp, col = oracle.csr_build(n, u, v)
+    return g, rp, col
+
+
+def close(a, b):
+    return np.allclose(a, b, rtol=RTOL, atol=ATOL)
+
+
+MODES = [
+    dict(mode=1, tpv=1), dict(mode=1, tpv=4), dict(mode=1, tpv=32),
+    dict(mode=1, direction=1), dict(mode=1, direction=2),
+    dict(mode=2, batch=64), dict(mode=2, batch=128), dict(mode=2, batch=256),
+    dict(mode=2, batch=64, direction=1), dict(mode=2, batch=64, direction=2),
+    dict(mode=2, batch=128, alpha=0.05), dict(mode=2, batch=64, alpha=50.0),
+]
+
+SMALL = {
+    "path": G.path(40), "cycle_odd": G.cycle(31), "cycle_even": G.cycle(30), "star": G.star(50),
+    "complete": G.complete(12), "k_ab": G.complete_bipartite(5, 9), "grid": G.grid(9, 13),
+    "hypercube": G.hypercube(6), "tree": G.random_tree(300, 3), "gnp": G.gnp(200, 0.04, 5),
+    "components": G.disjoint_union(G.path(7), G.gnp(60, 0.1, 2), G.star(5), G.complete(1)),
+    "isolated": G.disjoint_union(G.complete(1), G.complete(1), G.path(3)),
+}
+
+
+# ------------------------------------------------------------------ CSR builder
+@pytest.mark.parametrize("name", sorted(SMALL))
+def test_csr_builder_matches_oracle(nk, name):
+    n, u, v = SMALL[name]
+    rp, col = oracle.csr_build(n, u, v)
+    for graph in ((n, u, v), G.noisy((n, u, v), 1)):
+        g = nk.graph_from_edges(*graph)
+        grp, gcol = g.export_csr()
+        assert np.array_equal(grp, rp) and np.array_equal(gcol, col)
+    g = nk.graph_from_csr(rp, col, nk.CSR_VALIDATE)
+    assert g.info() == (n, len(col))
+
+
+def test_csr_canonicalise_and_validate(nk):
+    n, u, v = G.gnp(500, 0.02, 8)
+    rp, col = oracle.csr_build(n, u, v)
+    # one direction only, unsorted, duplicated, with loops: canonicalised on the GPU
+    nn, uu, vv = G.noisy((n, u, v), 4)
+    order = np.lexsort((vv, uu))
+    uu, vv = uu[order], vv[order]
+    raw_rp = np.zeros(n + 1, np.int64)
+    np.add.at(raw_rp, uu + 1, 1)
+    raw_rp = np.cumsum(raw_rp).astype(np.int32)
+    g = nk.graph_from_csr(raw_rp, vv, nk.CSR_CANONICALISE)
+    grp, gcol = g.export_csr()
+    assert np.array_equal(grp, rp) and np.array_equal(gcol, col)
+    with pytest.raises(nk.NkError) as e:
+        nk.graph_from_csr(raw_rp, vv, nk.CSR_VALIDATE)
+    assert e.value.rc == nk.ERR_GRAPH
+    bad = col.copy()
+    bad[0] = n  # out of range
+    with pytest.raises(nk.NkError):
+        nk.graph_from_csr(rp, bad, 0)
+    with pytest.raises(nk.NkError):
+        nk.graph_from_edges(3, np.array([0, 3]), np.array([1, 0]))
+
+
+def test_csr_long_rows(nk):
+    # rows longer than 32 and 4096 use the shared-memory and bitmap sorters
+    n = 20000
+    rng = np.random.default_rng(3)
+    u = np.concatenate([np.zeros(9000, np.int64), np.full(3000, 7), rng.integers(0, n, 5000)])
+    v = np.concatenate([rng.integers(0, n, 9000), rng.integers(0, n, 3000), rng.integers(0, n, 5000)])
+    rp, col = oracle.csr_build(n, u, v)
+    g = nk.graph_from_edges(n, u, v)
+    grp, gcol = g.export_csr()
+    assert np.array_equal(grp, rp) and np.array_equal(gcol, col)
+
+
+# ------------------------------------------------------------------ generators
+@pytest.mark.parametrize("kind,size,seed,params", [
+    ("er", 2000, 1, dict(avg_deg=8.0)), ("er", 1500, 3, dict(avg_deg=20.0)),
+    ("er", 7, 2, dict(avg_deg=10.0)), ("er", 1, 1, dict(avg_deg=8.0)),
+    ("ba", 5000, 1, dict(m0=8)), ("ba", 3000, 5, dict(m0=1)), ("ba", 1, 1, dict(m0=4)),
+    ("rmat", 12, 1, {}), ("rmat", 14, 7, dict(edge_factor=8, a=0.45, b=0.25, c=0.15)),
+])
+def test_generators_byte_identical(nk, kind, size, seed, params):
+    g = nk.graph_generate(kind, size, seed, **params)
+    n, rp, col = oracle.generate(kind, size, seed, **params)
+    grp, gcol = g.export_csr()
+    assert g.n == n
+    assert np.array_equal(grp, rp) and np.array_equal(gcol, col)
+
+
+def test_generators_full_size_configs(nk):
+    # R-MAT scale 18 edge factor 16 and BA n = 1e6, m0 = 8: byte-identical CSR
+    for kind, size, params in (("rmat", 18, {}), ("ba", 1000000, dict(m0=8))):
+        g = nk.graph_generate(kind, size, 1, **params)
+        n, rp, col = oracle.generate(kind, size, 1, **params)
+        grp, gcol = g.export_csr()
+        assert np.array_equal(grp, rp) and np.array_equal(gcol, col), kind
+        g.free()
+
+
+# ------------------------------------------------------------------ sampler
+@pytest.mark.parametrize("n,k,seed", [(1, 1, 1), (10, 10, 3), (1000, 1, 2), (5000, 1024, 2),
+                                      (262144, 1024, 2), (100000, 99999, 5), (70000, 4096, 0)])
+def test_sampler_matches_oracle(nk, n, k, seed):
+    assert np.array_equal(nk.sample_sources(n, seed, k), oracle.sample_sources(n, seed, k))
+
+
+# ------------------------------------------------------------------ forward sweep
+@pytest.mark.parametrize("name", sorted(SMALL))
+def test_sssp_bit_exact_small(nk, name):
+    g, rp, col = both(nk, SMALL[name])
+    n = len(rp) - 1
+    for s in range(0, n, max(1, n // 25)):
+        d, sg = nk.sssp(g, s)
+        d0, s0 = oracle.bfs(rp, col, s)
+        assert np.array_equal(d, d0) and np.array_equal(sg, s0), (name, s)
+
+
+def test_sssp_bit_exact_generated(nk):
+    for kind, size, params in (("er", 2000, dict(avg_deg=8.0)), ("rmat", 14, {}), ("ba", 20000, dict(m0=4))):
+        g = nk.graph_generate(kind, size, 1, **params)
+        n, rp, col = oracle.generate(kind, size, 1, **params)
+        for s in np.random.default_rng(0).integers(0, n, 12):
+            d, sg = nk.sssp(g, int(s))
+            d0, s0 = oracle.bfs(rp, col, int(s))
+            assert np.array_equal(d, d0) and np.array_equal(sg, s0), (kind, s)
+
+
+def test_sigma_near_limit_and_overflow(nk):
+    g, rp, col = both(nk, G.grid(34, 35))
+    d, sg = nk.sssp(g, 0)
+    d0, s0 = oracle.bfs(rp, col, 0)
+    assert np.array_equal(sg, s0) and int(sg[33 * 35 + 34]) == 14226520737620288370
+    g2, _, _ = both(nk, G.grid(35, 35))
+    with pytest.raises(nk.NkError) as e:
+        nk.sssp(g2, 0)
+    assert e.value.rc == nk.ERR_OVERFLOW
+    for opts in (nk.run_opts(mode=1), nk.run_opts(mode=2, batch=64)):
+        with pytest.raises(nk.NkError) as e:
+            nk.betweenness_sources(g2, np.array([0, 1], np.int32), 1.0, opts)
+        assert e.value.rc == nk.ERR_OVERFLOW
+
+
+# ------------------------------------------------------------------ betweenness
+@pytest.mark.parametrize("name", sorted(SMALL))
+def test_exact_small_graphs(nk, name):
+    g, rp, col = both(nk, SMALL[name])
+    want = oracle.betweenness_exact(rp, col)
+    assert close(nk.betweenness_exact(g), want)
+    n = len(rp) - 1
+    src = np.arange(n, dtype=np.int32)
+    for m in MODES:
+        got = nk.betweenness_sources(g, src, 0.5, nk.run_opts(**m))
+        assert close(got, want), (name, m)
+
+
+def test_exact_er_2000(nk):
+    # Erdos-Renyi n = 2000, average degree 8, seed 1, all 2000 sources
+    g = nk.graph_generate("er", 2000, 1, avg_deg=8.0)
+    n, rp, col = oracle.generate("er", 2000, 1, avg_deg=8.0)
+    want = oracle.betweenness_exact(rp, col)
+    assert close(nk.betweenness_exact(g), want)
+    for m in (dict(mode=1), dict(mode=2, batch=64), dict(mode=2, batch=256)):
+        assert close(nk.betweenness_sources(g, np.arange(n, dtype=np.int32), 0.5, nk.run_opts(**m)), want), m
+
+
+@pytest.mark.parametrize("m", MODES)
+def test_sampled_rmat_modes(nk, m):
+    g = nk.graph_generate("rmat", 13, 5)
+    n, rp, col = oracle.generate("rmat", 13, 5)
+    k = 333  # not a multiple of any batch size
+    want = oracle.betweenness_sampled(rp, col, 4, k)
+    got = nk.betweenness_sampled(g, 4, k, nk.run_opts(**m))
+    assert close(got, want), m
+
+
+def test_sampled_ba_and_isolated_sources(nk):
+    # R-MAT leaves many isolated vertices: sampled sources that are isolated count
+    g = nk.graph_generate("rmat", 11, 9, edge_factor=2)
+    n, rp, col = oracle.generate("rmat", 11, 9, edge_factor=2)
+    assert np.any(np.diff(rp)[oracle.sample_sources(n, 1, 500)] == 0)
+    assert close(nk.betweenness_sampled(g, 1, 500), oracle.betweenness_sampled(rp, col, 1, 500))
+    g = nk.graph_generate("ba", 30000, 2, m0=8)
+    n, rp, col = oracle.generate("ba", 30000, 2, m0=8)
+    assert close(nk.betweenness_sampled(g, 3, 200), oracle.betweenness_sampled(rp, col, 3, 200))
+
+
+def test_sampled_k_equals_n_is_exact(nk):
+    g, rp, col = both(nk, G.gnp(150, 0.05, 12))
+    assert close(nk.betweenness_sampled(g, 77, 150), oracle.betweenness_exact(rp, col))
+
+
+def test_deep_graph_falls_back_to_per_source(nk):
+    # a path of 3000 vertices is deeper than the batched form's level slabs
+    g, rp, col = both(nk, G.path(3000))
+    src = np.array([0, 5, 1499, 2999], np.int32)
+    want = oracle.betweenness_sources(rp, col, src, 1.0)
+    got = nk.betweenness_sources(g, src, 1.0, nk.run_opts(mode=2, batch=64))
+    assert close(got, want)
+
+
+def test_device_pointer_outputs(nk):
+    import torch
+    g = nk.graph_generate("ba", 4000, 3, m0=4)
+    n, rp, col = oracle.generate("ba", 4000, 3, m0=4)
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    nk.betweenness_sampled(g, 5, 100, nk.run_opts(mode=2), out=out)
+    assert close(out.cpu().numpy(), oracle.betweenness_sampled(rp, col, 5, 100))
+    src = torch.from_numpy(oracle.sample_sources(n, 5, 100)).cuda()
+    out2 = torch.empty(n, dtype=torch.float64, device="cuda")
+    nk.betweenness_sources(g, src, n / 200.0, nk.run_opts(mode=1), out=out2)
+    assert close(out2.cpu().numpy(), out.cpu().numpy())
+
+
+def test_argument_errors(nk):
+    g = nk.graph_generate("er", 100, 1, avg_deg=4.0)
+    for k in (0, 101):
+        with pytest.raises(nk.NkError) as e:
+            nk.betweenness_sampled(g, 1, k)
+        assert e.value.rc == nk.ERR_ARG
+    with pytest.raises(nk.NkError):
+        nk.sssp(g, 100)
+    with pytest.raises(nk.NkError):
+        nk.betweenness_sources(g, np.array([0, 100], np.int32), 1.0)
+    with pytest.raises(nk.NkError):
+        nk.betweenness_sampled(g, 1, 10, nk.run_opts(mode=2, batch=96))
+
+
+def test_bounded_wait_times_out_cleanly(nk):
+    assert nk.selftest_wait_timeout(50_000_000) == nk.ERR_TIMEOUT
+    g = nk.graph_generate("er", 200, 2, avg_deg=5.0)
+    n, rp, col = oracle.generate("er", 200, 2, avg_deg=5.0)
+    assert close(nk.betweenness_exact(g), oracle.betweenness_exact(rp, col))
+
+
+def test_autotune_then_run(nk):
+    g = nk.graph_generate("rmat", 12, 3)
+    n, rp, col = oracle.generate("rmat", 12, 3)
+    best = nk.autotune(g, 2, 300)
+    assert best.batch in (64, 128, 256) and best.alpha > 0
+    assert close(nk.betweenness_sampled(g, 2, 300), oracle.betweenness_sampled(rp, col, 2, 300))
