@@ -1,0 +1,468 @@
+#!/usr/bin/env python3
+"""Sampled-betweenness benchmark on one GB300 (one JSON line on stdout).
+
+A step is one pass of the whole hot path on the graph resident in HBM: source sampling,
+the forward (sigma) and backward (delta) sweeps of every source, and the score
+reduction and scaling - one nk_betweenness_sampled call.  Graph generation and the CSR
+build are set-up (timed separately, reported as `generation_ms`).
+
+Default workload (N = 1): R-MAT scale 18, edge factor 16, (a,b,c) = (0.57,0.19,0.19),
+graph seed 1, symmetrised / no loops / no duplicates, k = 1024 sources from sampler seed
+2, scores scaled n/(2k); batched multi-source form, autotuned.  The same run also times
+the plain per-source form (`per_source`), the end-to-end call with host buffers
+(`e2e`), a short continuous-batching serving load (`serving`), and the CPU oracle on a
+bounded sample of the same workload (`cpu_baseline`).
+
+GTEPS = m * k / t with m the undirected edges after canonicalisation.
+Under torchrun (N > 1) each rank runs its own k sources (sampler seed 2 + rank) on its
+own GPU: independent problems, no data-path collective ("weak" scaling).
+`--impl reference` times the CPU oracle (plain sequential Brandes) on the same config.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sampled-betweenness GTEPS on 1 GB300 (batched/served vs per-source); p50/p99 latency"
+UNIT = "GTEPS"
+
+CONFIGS = {
+    "rmat18": dict(kind="rmat", size=18, params={}, k=1024,
+                   workload="sampled betweenness, R-MAT scale 18, edge factor 16, "
+                            "(a,b,c)=(0.57,0.19,0.19), k=1024"),
+    "er2000": dict(kind="er", size=2000, params=dict(avg_deg=8.0), k=2000,
+                   workload="exact betweenness (all 2000 sources), Erdos-Renyi n=2000, avg degree 8"),
+    "ba1m": dict(kind="ba", size=1000000, params=dict(m0=8), k=4096,
+                 workload="sampled betweenness, Barabasi-Albert n=1e6, m0=8, k=4096"),
+    "rmat24": dict(kind="rmat", size=24, params={}, k=8192,
+                   workload="sampled betweenness, R-MAT scale 24, edge factor 16, "
+                            "(a,b,c)=(0.57,0.19,0.19), k=8192"),
+}
+GRAPH_SEED, SAMPLE_SEED = 1, 2
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--config", default="rmat18", choices=sorted(CONFIGS))
+    p.add_argument("--serve-requests", type=int, default=200)
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-per-source", action="store_true")
+    p.add_argument("--batch", type=int, default=0)
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ distributed plumbing
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if args.impl == "ours":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+def algorithmic_bytes_per_launch(n, A, B):
+    """Batched form, per launch of B sources: the CSR streamed once per sweep
+    (2 sweeps x (4A + 4n)), the per-level bitsets 24n ... in the per-source figure
+    (8A + 24n)/B + 34n of the hot-path byte model, times the B sources of a launch."""
+    return (8.0 * A + 24.0 * n) + 34.0 * n * B
+
+
+def per_source_bytes(n, A):
+    """Per-source form, per source: 8A + 64n bytes."""
+    return 8.0 * A + 64.0 * n
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def serving_load(nk, torch, n_req, seed=3):
+    """Mixed-size serving load: graph type uniform over ER (avg deg 8), BA (m0=4) and
+    R-MAT (edge factor 16); n log-uniform in [1e3, 1e6] (R-MAT scale = round(log2 n));
+    k log-uniform in [64, 1024], at most n.  Capacity C from a closed-loop run, then
+    Poisson arrivals at 0.7 C."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n_req):
+        kind = ["er", "ba", "rmat"][int(rng.integers(0, 3))]
+        n = int(round(math.exp(rng.uniform(math.log(1e3), math.log(1e6)))))
+        k = int(round(math.exp(rng.uniform(math.log(64), math.log(1024)))))
+        gseed, sseed = 1000003 * seed + 2 * i, 1000003 * seed + 2 * i + 1
+        if kind == "er":
+            g = nk.graph_generate("er", n, gseed, avg_deg=8.0)
+        elif kind == "ba":
+            g = nk.graph_generate("ba", n, gseed, m0=4)
+        else:
+            g = nk.graph_generate("rmat", max(10, int(round(math.log2(n)))), gseed)
+        reqs.append((g, sseed, min(k, g.n)))
+    # closed loop: everything submitted at once
+    srv = nk.Server()
+    t0 = time.perf_counter()
+    ids = [srv.submit(g, s, k)[0] for g, s, k in reqs]
+    for i in ids:
+        assert srv.wait(i, 600.0) == 0
+    closed_s = time.perf_counter() - t0
+    srv.close()
+    cap = len(reqs) / closed_s
+    # open loop at 0.7 C
+    lam = 0.7 * cap
+    gaps = rng.exponential(1.0 / lam, len(reqs))
+    srv = nk.Server()
+    t0 = time.perf_counter()
+    next_t = t0
+    ids = []
+    for (g, s, k), gap in zip(reqs, gaps):
+        next_t += gap
+        while time.perf_counter() < next_t:
+            time.sleep(min(0.0005, max(0.0, next_t - time.perf_counter())))
+        ids.append(srv.submit(g, s, k)[0])
+    for i in ids:
+        assert srv.wait(i, 600.0) == 0
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    for g, _, _ in reqs:
+        g.free()
+    return {"requests": len(reqs), "capacity_req_per_s": cap, "arrival_rate_req_per_s": lam,
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+            "gteps": st["edges_x_sources"] / wall / 1e9, "wall_s": wall,
+            "peak_inflight": st["peak_inflight"], "peak_bytes": st["peak_bytes"],
+            "closed_loop_gteps": st["edges_x_sources"] / closed_s / 1e9}
+
+
+def cpu_baseline(cfg, seconds, rank_seed):
+    """The oracle, as it stands, on one host core: Brandes on the first sources of the
+    same sampled set of the oracle's own copy of the graph, until `seconds` pass."""
+    import numpy as np
+    import oracle
+    n, rp, col = oracle.generate(cfg["kind"], cfg["size"], GRAPH_SEED, **cfg["params"])
+    m = len(col) // 2
+    if cfg["kind"] == "er" and cfg["k"] == n:
+        src = np.arange(n, dtype=np.int32)
+    else:
+        src = oracle.sample_sources(n, rank_seed, cfg["k"])
+    done, t0 = 0, time.perf_counter()
+    chunk = 2
+    while done < len(src):
+        oracle.betweenness_sources(rp, col, src[done:done + chunk], 1.0)
+        done += min(chunk, len(src) - done)
+        if time.perf_counter() - t0 >= seconds:
+            break
+    t = time.perf_counter() - t0
+    return {"value": m * done / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} of the {len(src)} sources of the same workload, "
+                      f"oracle-generated graph, {t:.1f} s on 1 host core"}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    cfg = CONFIGS[args.config]
+    n, rp, col = oracle.generate(cfg["kind"], cfg["size"], GRAPH_SEED, **cfg["params"])
+    m = len(col) // 2
+    src = (np.arange(n, dtype=np.int32) if cfg["kind"] == "er" and cfg["k"] == n
+           else oracle.sample_sources(n, SAMPLE_SEED, cfg["k"]))
+    # per step: a bounded sample of the workload, about 1.5 s of single-core work
+    t0 = time.perf_counter()
+    oracle.betweenness_sources(rp, col, src[:1], 1.0)
+    per_src = max(time.perf_counter() - t0, 1e-6)
+    per_step = max(1, min(len(src), int(1.5 / per_src)))
+    for w in range(args.warmup):
+        oracle.betweenness_sources(rp, col, src[:min(per_step, 2)], 1.0)
+    times = []
+    for i in range(args.steps):
+        sl = src[(i * per_step) % len(src):][:per_step]
+        t0 = time.perf_counter()
+        oracle.betweenness_sources(rp, col, sl, 1.0)
+        times.append((time.perf_counter() - t0, len(sl)))
+    tot_t = sum(t for t, _ in times)
+    tot_s = sum(s for _, s in times)
+    value = m * tot_s / tot_t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_t / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["workload"], "n": n, "m": m, "k": cfg["k"],
+                       "sources_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} sources per step of the {len(src)}-source workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_1403_3005_gb300 import nk
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    nk.set_stream(stream)
+    cfg = CONFIGS[args.config]
+    sseed = SAMPLE_SEED + rank
+    exact = cfg["kind"] == "er" and cfg["k"] == cfg["size"]
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    g = nk.graph_generate(cfg["kind"], cfg["size"], GRAPH_SEED, **cfg["params"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    gen_ms = ev0.elapsed_time(ev1)
+    n, A = g.info()
+    m = A // 2
+    k = cfg["k"]
+
+    if exact:
+        opts = nk.run_opts(mode=nk.MODE_BATCHED, batch=args.batch or 64)
+        src_dev = torch.arange(n, dtype=torch.int32, device="cuda")
+    else:
+        opts = nk.autotune(g, sseed, k) if not args.batch else nk.run_opts(mode=nk.MODE_BATCHED, batch=args.batch)
+        src_dev = None
+    opts.flags |= nk.RUN_TIME_KERNELS
+    scores = torch.empty(n, dtype=torch.float64, device="cuda")
+
+    def step(o):
+        if exact:
+            nk.betweenness_sources(g, src_dev, 0.5, o, out=scores)
+        else:
+            nk.betweenness_sampled(g, sseed, k, o, out=scores)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        step(opts)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, L2 flushed between steps (outside the events)
+    barrier(world)
+    torch.cuda.synchronize()
+    step_ms, kern_ms, launches = [], 0.0, 0
+    l0 = nk.launch_count()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0.record(stream)
+            step(opts)
+            ev1.record(stream)
+            ev1.synchronize()
+            step_ms.append(ev0.elapsed_time(ev1))
+            st = nk.last_run_stats()
+            kern_ms += st["kernel_ms"]
+            launches += st["launches"]
+    torch.cuda.synchronize()
+    barrier(world)
+    gpu_launches = nk.launch_count() - l0
+    stats = nk.last_run_stats()
+    total_ms = max_over_ranks(sum(step_ms), world)
+    ms_per_step = total_ms / args.steps
+    value = world * m * k * args.steps / (total_ms / 1e3) / 1e9
+
+    # ---- dominant kernel roofline (batched sweep kernel, per launch)
+    B = stats["batch"]
+    peak, peak_kind = measured_peaks()
+    per_launch_ms = kern_ms / max(launches, 1)
+    alg = algorithmic_bytes_per_launch(n, A, B)
+    achieved = alg / (per_launch_ms / 1e3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", f"k_batch_{args.config}_traffic.json")
+    if os.path.exists(prof):
+        try:
+            with open(prof) as f:
+                pj = json.load(f)
+            if pj.get("batch") == B:
+                traffic = pj.get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": f"k_batch<W={B // 64}>", "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": alg, "avg_launch_ms": per_launch_ms}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": cfg["workload"], "n": n, "m": m, "arcs": A, "k": k,
+                      "graph_seed": GRAPH_SEED, "sample_seed": sseed, "form": "batched",
+                      "batch": B, "alpha": stats["alpha"], "max_depth": stats["max_depth"],
+                      "td_levels": stats["td_levels"], "bu_levels": stats["bu_levels"],
+                      "l2": "flushed (256 MiB write) between steps", "sigma": "uint64",
+                      "parallelism": f"sources split over {world} GPU(s), no collective"},
+           "roofline": roofline, "gpu_launches": int(gpu_launches),
+           "clocks": clk.summary(), "generation_ms": gen_ms}
+
+    # ---- plain per-source form on the same workload (the baseline it beats)
+    if not args.no_per_source and rank == 0:
+        po = nk.run_opts(mode=nk.MODE_PER_SOURCE, flags=nk.RUN_TIME_KERNELS)
+        step(po)
+        torch.cuda.synchronize()
+        flush.zero_()
+        ev0.record(stream)
+        step(po)
+        ev1.record(stream)
+        ev1.synchronize()
+        t = ev0.elapsed_time(ev1)
+        ps = nk.last_run_stats()
+        plm = ps["kernel_ms"] / max(ps["launches"], 1)
+        ps_value = m * k / (t / 1e3) / 1e9
+        out["per_source"] = {"value": ps_value, "unit": UNIT, "ms_per_step": t,
+                             "tpv": ps["tpv"], "avg_launch_ms": plm,
+                             "achieved_gbs": per_source_bytes(n, A) / (plm / 1e3) / 1e9,
+                             "batched_speedup": (value / world) / ps_value}
+
+    # ---- end to end through the C ABI with host buffers (pinned)
+    rp, col = g.export_csr()
+    rp_p = torch.from_numpy(rp).pin_memory()
+    col_p = torch.from_numpy(col).pin_memory()
+    sc_p = torch.empty(n, dtype=torch.float64).pin_memory()
+    eo = nk.run_opts(mode=nk.MODE_BATCHED, batch=B, alpha=stats["alpha"])
+    src_h = np.arange(n, dtype=np.int32) if exact else None
+
+    def e2e_step():
+        g2 = nk.graph_from_csr(rp_p.numpy(), col_p.numpy(), 0)
+        if exact:
+            nk.betweenness_sources(g2, src_h, 0.5, eo, out=sc_p.numpy())
+        else:
+            nk.betweenness_sampled(g2, sseed, k, eo, out=sc_p.numpy())
+        g2.free()
+
+    e2e_step()
+    e2e_ms = []
+    for _ in range(max(2, min(args.steps, 5))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_tot = max_over_ranks(sum(e2e_ms), world)
+    out["e2e"] = {"value": world * m * k * len(e2e_ms) / (e2e_tot / 1e3) / 1e9, "unit": UNIT,
+                  "h2d_bytes_per_step": 4 * (n + 1) + 4 * A + (4 * n if exact else 0),
+                  "d2h_bytes_per_step": 8 * n, "ms_per_step": e2e_tot / len(e2e_ms)}
+
+    # ---- serving load (continuous batching), rank 0
+    if not args.no_serve and rank == 0 and args.serve_requests > 0:
+        out["serving"] = serving_load(nk, torch, args.serve_requests)
+
+    # ---- the oracle on the host cores (rank 0, N = 1 only)
+    if not args.no_cpu and rank == 0 and world == 1:
+        out["cpu_baseline"] = cpu_baseline(cfg, args.cpu_seconds, sseed)
+
+    g.free()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        rc = run_reference(args, world, rank)
+    else:
+        rc = run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

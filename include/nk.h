@@ -217,6 +217,9 @@ int nk_set_wait_limit_ns(uint64_t ns);
  * (and the CUDA context stays usable). */
 int nk_selftest_wait_timeout(uint64_t limit_ns);
 
+/* Number of kernels this library has launched in this process (all entry points). */
+uint64_t nk_launch_count(void);
+
 const char *nk_last_error(void);
 const char *nk_version(void);
 

@@ -47,6 +47,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kErrDepth = 100;  // internal status: BFS deeper than the level slabs
 constexpr unsigned FULL = 0xffffffffu;
+constexpr int kChunk = kHeavyChunk;  // arcs per work item; longer rows are split
 
 struct BArgs {
     int32_t n;
@@ -71,6 +72,12 @@ struct BArgs {
     uint64_t limit_ns;
     double alpha;
     int dir;
+    // vertices of degree > kChunk are split into chunks of kChunk arcs
+    const int32_t *hv;           // [H] heavy vertices
+    const int32_t *hfirst;       // [H+1] first chunk of each heavy vertex
+    const int32_t *chunk_h;      // [C] heavy index of each chunk
+    int32_t H, C;
+    unsigned long long *part;    // [C][B] per-chunk partial sums (uint64 or double)
 };
 
 template <int W> struct Bits {
@@ -262,6 +269,39 @@ __device__ __forceinline__ void for_level(const BArgs &a, int qo, int nq,
     }
 }
 
+// Work on the chunks of heavy vertices: fn(c, h, j0, j1) per chunk, with the whole warp.
+template <class Fn> __device__ __forceinline__ void for_chunks(const BArgs &a, Fn fn)
+{
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long c = wid; c < a.C; c += nw) {
+        const int i = __ldg(a.chunk_h + c);
+        const int h = __ldg(a.hv + i);
+        const int j0 = __ldg(a.rp + h) + (int)(c - __ldg(a.hfirst + i)) * kChunk;
+        const int j1 = min(j0 + kChunk, __ldg(a.rp + h + 1));
+        fn((int)c, h, j0, j1);
+    }
+}
+
+// fn(i, h, c0, c1) per heavy vertex (chunks [c0, c1)), with the whole warp.
+template <class Fn> __device__ __forceinline__ void for_heavy(const BArgs &a, Fn fn)
+{
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long i = wid; i < a.H; i += nw)
+        fn((int)i, __ldg(a.hv + i), __ldg(a.hfirst + i), __ldg(a.hfirst + i + 1));
+}
+
+template <int W>
+__device__ __forceinline__ void store_part(const BArgs &a, int c, const unsigned long long (&acc)[2 * W])
+{
+    unsigned long long *row = a.part + (size_t)c * (64 * W) + (threadIdx.x & 31);
+#pragma unroll
+    for (int k = 0; k < 2 * W; ++k) row[32 * k] = acc[k];
+}
+
+__device__ __forceinline__ bool heavy(const BArgs &a, int v) { return deg_of(a.rp, v) > kChunk; }
+
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
 {
@@ -279,6 +319,14 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
         act.w[q] = left >= 64 ? ~0ull : (left <= 0 ? 0ull : ((1ull << left) - 1));
     }
     bool ovf = false;
+    auto flush_counts = [&](int lvl) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (bc.v) atomicAdd(a.vcnt + lvl, bc.v);
+            if (bc.mf) atomicAdd(a.mfv + lvl, bc.mf);
+            if (bc.dmu) atomicAdd(a.dmu + lvl, bc.dmu);
+        }
+    };
 
     // ---- init: empty visited sets, F_0 and F_1, queue marks, level-0..2 counters
     for (size_t i = tid; i < slab; i += nthr) {
@@ -340,11 +388,12 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
         bool queued = false;
         int nq1 = 0;
         if (use_bu) {
-            // ---- bottom-up: every vertex with unvisited sources pulls from level d
+            // ---- bottom-up (a): light vertices with unvisited sources pull from level d;
+            //      chunks of heavy vertices store partial sums
             for (long long base = wid * 32; base < a.n; base += nw * 32) {
                 const long long v = base + lane;
                 Bits<W> vv = act;
-                if (v < a.n) vv = load_bits<W>(a.vis + (size_t)v * W);
+                if (v < a.n && !heavy(a, (int)v)) vv = load_bits<W>(a.vis + (size_t)v * W);
                 unsigned m = __ballot_sync(FULL, any_bits<W>(andnot<W>(act, vv)));
                 while (m) {
                     const int t = __ffs(m) - 1;
@@ -361,20 +410,45 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
                     if (any_bits<W>(nb)) settle<W>(a, w, vold, nb, act, acc, Fn, &bc);
                 }
             }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                if (bc.v) atomicAdd(a.vcnt + d + 1, bc.v);
-                if (bc.mf) atomicAdd(a.mfv + d + 1, bc.mf);
-                if (bc.dmu) atomicAdd(a.dmu + d + 1, bc.dmu);
-            }
+            for_chunks(a, [&](int c, int h, int j0, int j1) {
+                const Bits<W> u = andnot<W>(act, load_bits<W>(a.vis + (size_t)h * W));
+                if (!any_bits<W>(u)) return;
+                unsigned long long acc[2 * W];
+                double facc[2 * W];
+#pragma unroll
+                for (int k = 0; k < 2 * W; ++k) acc[k] = 0;
+                gather<W, false>(a, j0, j1, Fd, u, acc, facc, ovf);
+                store_part<W>(a, c, acc);
+            });
+            if (a.H > 0 && !dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+            // ---- bottom-up (b): heavy vertices sum their chunks in chunk order
+            for_heavy(a, [&](int i, int h, int c0, int c1) {
+                const Bits<W> vold = load_bits<W>(a.vis + (size_t)h * W);
+                if (!any_bits<W>(andnot<W>(act, vold))) return;
+                unsigned long long acc[2 * W];
+#pragma unroll
+                for (int k = 0; k < 2 * W; ++k) acc[k] = 0;
+                for (int c = c0; c < c1; ++c) {
+                    const unsigned long long *row = a.part + (size_t)c * B + lane;
+#pragma unroll
+                    for (int k = 0; k < 2 * W; ++k) {
+                        const unsigned long long y = acc[k] + __ldcg(row + 32 * k);
+                        ovf |= y < acc[k];
+                        acc[k] = y;
+                    }
+                }
+                const Bits<W> nb = nonzero_bits<W>(acc);
+                if (any_bits<W>(nb)) settle<W>(a, h, vold, nb, act, acc, Fn, &bc);
+            });
+            flush_counts(d + 1);
             if (tid == 0) a.qoff[d + 1] = -1;
             if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
         } else {
-            // ---- top-down (a): push the frontier's bits, queue each new vertex once
-            for_level<W>(a, qo, nq, Fd, [&](int v) {
+            // ---- top-down (a): push the frontier's bits, queue each new vertex once;
+            //      heavy frontier vertices push chunk by chunk
+            auto push = [&](int v, int j0, int j1) {
                 const Bits<W> f = load_bits<W>(Fd + (size_t)v * W);
-                const int beg = __ldg(a.rp + v), end = __ldg(a.rp + v + 1);
-                for (int j = beg + lane; j < end; j += 32) {
+                for (int j = j0 + lane; j < j1; j += 32) {
                     const int c = __ldg(a.col + j);
                     const Bits<W> m = andnot<W>(f, load_bits<W>(a.vis + (size_t)c * W));
                     if (!any_bits<W>(m)) continue;
@@ -389,12 +463,20 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
                         if (qtail + pos < a.qcap) a.queue[qtail + pos] = c;
                     }
                 }
+            };
+            for_level<W>(a, qo, nq, Fd, [&](int v) {
+                if (heavy(a, v)) return;
+                push(v, __ldg(a.rp + v), __ldg(a.rp + v + 1));
+            });
+            for_chunks(a, [&](int c, int h, int j0, int j1) {
+                if (any_bits<W>(load_bits<W>(Fd + (size_t)h * W))) push(h, j0, j1);
             });
             if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
             // ---- top-down (b): every new vertex pulls sigma for its new bits
             nq1 = __ldcg(a.qcnt + d + 1);
             queued = qtail + nq1 <= a.qcap;
             for_level<W>(a, queued ? (int)qtail : -1, nq1, Fn, [&](int w) {
+                if (heavy(a, w)) return;
                 const Bits<W> t = load_bits<W>(Fn + (size_t)w * W);
                 const Bits<W> vold = load_bits<W>(a.vis + (size_t)w * W);
                 unsigned long long acc[2 * W];
@@ -404,12 +486,37 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
                 gather<W, false>(a, __ldg(a.rp + w), __ldg(a.rp + w + 1), Fd, t, acc, facc, ovf);
                 settle<W>(a, w, vold, t, act, acc, nullptr, &bc);
             });
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                if (bc.v) atomicAdd(a.vcnt + d + 1, bc.v);
-                if (bc.mf) atomicAdd(a.mfv + d + 1, bc.mf);
-                if (bc.dmu) atomicAdd(a.dmu + d + 1, bc.dmu);
-            }
+            for_chunks(a, [&](int c, int h, int j0, int j1) {
+                const Bits<W> t = load_bits<W>(Fn + (size_t)h * W);
+                if (!any_bits<W>(t)) return;
+                unsigned long long acc[2 * W];
+                double facc[2 * W];
+#pragma unroll
+                for (int k = 0; k < 2 * W; ++k) acc[k] = 0;
+                gather<W, false>(a, j0, j1, Fd, t, acc, facc, ovf);
+                store_part<W>(a, c, acc);
+            });
+            if (a.H > 0 && !dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+            // ---- top-down (c): heavy new vertices sum their chunks in chunk order
+            for_heavy(a, [&](int i, int h, int c0, int c1) {
+                const Bits<W> t = load_bits<W>(Fn + (size_t)h * W);
+                if (!any_bits<W>(t)) return;
+                const Bits<W> vold = load_bits<W>(a.vis + (size_t)h * W);
+                unsigned long long acc[2 * W];
+#pragma unroll
+                for (int k = 0; k < 2 * W; ++k) acc[k] = 0;
+                for (int c = c0; c < c1; ++c) {
+                    const unsigned long long *row = a.part + (size_t)c * B + lane;
+#pragma unroll
+                    for (int k = 0; k < 2 * W; ++k) {
+                        const unsigned long long y = acc[k] + __ldcg(row + 32 * k);
+                        ovf |= y < acc[k];
+                        acc[k] = y;
+                    }
+                }
+                settle<W>(a, h, vold, t, act, acc, nullptr, &bc);
+            });
+            flush_counts(d + 1);
             if (tid == 0) a.qoff[d + 1] = queued ? (int)qtail : -1;
             if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
         }
@@ -447,14 +554,8 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
         const unsigned long long *Fs = a.F + (size_t)(l + 1) * slab;
         const int ql = __ldcg(a.qoff + l);
         const int nl = ql >= 0 ? __ldcg(a.qcnt + l) : 0;
-        for_level<W>(a, ql, nl, Fl, [&](int v) {
-            const Bits<W> mv = load_bits<W>(Fl + (size_t)v * W);
-            unsigned long long acc[2 * W];
-            double facc[2 * W];
-#pragma unroll
-            for (int k = 0; k < 2 * W; ++k) facc[k] = 0.0;
-            bool dummy = false;
-            gather<W, true>(a, __ldg(a.rp + v), __ldg(a.rp + v + 1), Fs, mv, acc, facc, dummy);
+        // delta/psi/score of vertex v from its successor sums facc (whole warp)
+        auto finish = [&](int v, const Bits<W> &mv, const double (&facc)[2 * W]) {
             double part = 0.0;
             unsigned long long *row = a.sp + (size_t)v * B + lane;
 #pragma unroll
@@ -468,6 +569,44 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
             }
             part = dev::group_sum<32>(part);
             if (lane == 0 && part != 0.0) a.scores[v] += part;
+        };
+        for_level<W>(a, ql, nl, Fl, [&](int v) {
+            if (heavy(a, v)) return;
+            const Bits<W> mv = load_bits<W>(Fl + (size_t)v * W);
+            unsigned long long acc[2 * W];
+            double facc[2 * W];
+#pragma unroll
+            for (int k = 0; k < 2 * W; ++k) facc[k] = 0.0;
+            bool dummy = false;
+            gather<W, true>(a, __ldg(a.rp + v), __ldg(a.rp + v + 1), Fs, mv, acc, facc, dummy);
+            finish(v, mv, facc);
+        });
+        for_chunks(a, [&](int c, int h, int j0, int j1) {
+            const Bits<W> mv = load_bits<W>(Fl + (size_t)h * W);
+            if (!any_bits<W>(mv)) return;
+            unsigned long long acc[2 * W];
+            double facc[2 * W];
+#pragma unroll
+            for (int k = 0; k < 2 * W; ++k) facc[k] = 0.0;
+            bool dummy = false;
+            gather<W, true>(a, j0, j1, Fs, mv, acc, facc, dummy);
+#pragma unroll
+            for (int k = 0; k < 2 * W; ++k) acc[k] = (unsigned long long)__double_as_longlong(facc[k]);
+            store_part<W>(a, c, acc);
+        });
+        if (a.H > 0 && !dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+        for_heavy(a, [&](int i, int h, int c0, int c1) {
+            const Bits<W> mv = load_bits<W>(Fl + (size_t)h * W);
+            if (!any_bits<W>(mv)) return;
+            double facc[2 * W];
+#pragma unroll
+            for (int k = 0; k < 2 * W; ++k) facc[k] = 0.0;
+            for (int c = c0; c < c1; ++c) {
+                const unsigned long long *row = a.part + (size_t)c * B + lane;
+#pragma unroll
+                for (int k = 0; k < 2 * W; ++k) facc[k] += __longlong_as_double((long long)__ldcg(row + 32 * k));
+            }
+            finish(h, mv, facc);
         });
         if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
     }
@@ -488,10 +627,17 @@ template <int W> int blocks_per_sm()
 struct Layout {
     int W, B, lcap;
     int64_t qcap;
-    size_t off_F, off_vis, off_sp, off_qmark, off_queue, off_cnt, total;
+    size_t off_F, off_vis, off_sp, off_qmark, off_queue, off_cnt, off_part, total;
 };
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// chunk count of the heavy table (an upper bound before the table is built)
+int64_t chunk_count(const nk_graph *g)
+{
+    if (g->heavy_H >= 0) return g->heavy_C;
+    return g->A / kChunk + (g->max_deg > kChunk ? g->n : 0);
+}
 
 Layout layout(const nk_graph *g, int B, int lcap)
 {
@@ -514,6 +660,8 @@ Layout layout(const nk_graph *g, int B, int lcap)
     o = align_up(o + (size_t)L.qcap * 4);
     L.off_cnt = o;
     o = align_up(o + (size_t)(lcap + 3) * (3 * 4 + 2 * 8));
+    L.off_part = o;
+    o = align_up(o + (size_t)chunk_count(g) * B * 8);
     L.total = o;
     return L;
 }
@@ -540,6 +688,7 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
                    const RunCfg &cfg, RunStats *st, cudaStream_t s)
 {
     constexpr int B = 64 * W;
+    NK_TRY(build_heavy(g, s));
     DevBuf *ws = scratch(cfg, g);
     const int lcap = cfg.lcap > 0 ? std::min(cfg.lcap, std::max(g->n, 4)) : choose_lcap(g, B, ws);
     if (lcap < 4) return set_error(NK_ERR_NOMEM, "not enough device memory for a batch of %d sources", B);
@@ -570,6 +719,12 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
     a.qcnt = a.vcnt + lv;
     a.qoff = a.qcnt + lv;
     a.scores = d_scores;
+    a.hv = g->heavy[0].as<int32_t>();
+    a.hfirst = g->heavy[1].as<int32_t>();
+    a.chunk_h = g->heavy[2].as<int32_t>();
+    a.H = g->heavy_H;
+    a.C = g->heavy_C;
+    a.part = reinterpret_cast<unsigned long long *>(base + L.off_part);
     a.limit_ns = cfg.limit_ns ? cfg.limit_ns : wait_limit_ns();
     a.alpha = cfg.alpha > 0 ? cfg.alpha : 1.0;
     a.dir = cfg.direction;
@@ -588,6 +743,7 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
         a.ctrl = ctrls + bi;
         void *args[] = {&a};
         NK_CUDA(cudaLaunchCooperativeKernel((const void *)k_batch<W>, dim3(grid), dim3(kThreads), args, 0, s));
+        ::nk::count_launch();
     }
     if (cfg.time_kernels) NK_CUDA(cudaEventRecord(e1, s));
     std::vector<Ctrl> h(nb);

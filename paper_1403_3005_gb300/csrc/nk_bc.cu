@@ -102,6 +102,7 @@ int bc_entry(const nk_graph *gc, const int32_t *src, int32_t k, bool sample, uin
     } else if (!src) {
         NK_TRY(dsrc.alloc(sizeof(int32_t) * k, s));
         k_iota<<<std::max(1, std::min((k + 255) / 256, 8 * num_sms())), 256, 0, s>>>(dsrc.as<int32_t>(), k);
+        ::nk::count_launch();
         NK_CUDA(cudaGetLastError());
         d_src = dsrc.as<int32_t>();
     } else {
@@ -115,6 +116,7 @@ int bc_entry(const nk_graph *gc, const int32_t *src, int32_t k, bool sample, uin
         NK_TRY(flag.alloc(sizeof(int), s));
         NK_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
         k_check_src<<<std::max(1, std::min((k + 255) / 256, 8 * num_sms())), 256, 0, s>>>(d_src, k, n, flag.as<int>());
+        ::nk::count_launch();
         int hb = 0;
         NK_CUDA(cudaMemcpyAsync(&hb, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         NK_CUDA(cudaStreamSynchronize(s));

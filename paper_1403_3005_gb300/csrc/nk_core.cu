@@ -29,6 +29,8 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line)
                      line);
 }
 
+std::atomic<uint64_t> g_launches{0};
+
 // ---------------------------------------------------------------- stream / limits
 static std::atomic<cudaStream_t> g_stream{nullptr};
 static std::atomic<uint64_t> g_wait_ns{10ull * 1000 * 1000 * 1000};
@@ -157,15 +159,18 @@ int scan_rec(const int64_t *in, int64_t *out, int64_t count, cudaStream_t st)
     const int64_t tiles = (count + kTile - 1) / kTile;
     if (tiles == 1) {
         k_scan_tile<<<1, kScanThreads, 0, st>>>(in, out, nullptr, count);
+        ::nk::count_launch();
         NK_CUDA(cudaGetLastError());
         return NK_OK;
     }
     Tmp sums;
     NK_TRY(sums.alloc(sizeof(int64_t) * tiles, st));
     k_scan_tile<<<(unsigned)tiles, kScanThreads, 0, st>>>(in, out, sums.as<int64_t>(), count);
+    ::nk::count_launch();
     NK_CUDA(cudaGetLastError());
     NK_TRY(scan_rec(sums.as<int64_t>(), sums.as<int64_t>(), tiles, st));
     k_scan_add<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(out, sums.as<int64_t>(), count);
+    ::nk::count_launch();
     NK_CUDA(cudaGetLastError());
     return NK_OK;
 }
@@ -186,6 +191,7 @@ int scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t count, int64_t *
     if (total) {
         if (count > 0) {
             k_scan_total<<<1, 1, 0, st>>>(last, out + count - 1, 1, total);
+            ::nk::count_launch();
             NK_CUDA(cudaGetLastError());
         } else {
             NK_CUDA(cudaMemsetAsync(total, 0, sizeof(int64_t), st));
@@ -210,6 +216,7 @@ int scale_vector(double *d, int32_t n, double scale, cudaStream_t s)
     int blocks = (int)((n + 255) / 256);
     if (blocks > 8 * num_sms()) blocks = 8 * num_sms();
     k_scale<<<blocks, 256, 0, s>>>(d, n, scale);
+    ::nk::count_launch();
     NK_CUDA(cudaGetLastError());
     return NK_OK;
 }
@@ -244,6 +251,8 @@ const char *nk_last_error(void) { return t_err.c_str(); }
 
 const char *nk_version(void) { return "nk-gb300 0.1 (sm_103a)"; }
 
+uint64_t nk_launch_count(void) { return g_launches.load(); }
+
 int nk_set_stream(void *s)
 {
     g_stream.store(static_cast<cudaStream_t>(s));
@@ -267,6 +276,7 @@ int nk_selftest_wait_timeout(uint64_t limit_ns)
     int *flag = buf.as<int>(), *status = flag + 1;
     NK_CUDA(cudaMemsetAsync(flag, 0, 2 * sizeof(int), st));
     k_wait_flag<<<1, 1, 0, st>>>(flag, status, limit_ns);
+    ::nk::count_launch();
     NK_CUDA(cudaGetLastError());
     int h = 1;
     NK_CUDA(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -18,12 +18,15 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <vector>
 
 #include "nk_device.cuh"
 #include "nk_internal.h"
 
 namespace nk {
 namespace {
+
+int finish_graph(nk_graph *g, cudaStream_t st, int *d_maxdeg);
 
 constexpr int kMidMax = 4096;           // rows up to this length: shared-memory bitonic
 constexpr int kWinBits = 1 << 18;       // bitmap window for long rows (32 KiB)
@@ -388,7 +391,7 @@ int finish_graph(nk_graph *g, cudaStream_t st, int *d_maxdeg)
     NK_CUDA(cudaMemcpyAsync(&h, d_maxdeg, sizeof(int), cudaMemcpyDeviceToHost, st));
     NK_CUDA(cudaStreamSynchronize(st));
     g->max_deg = h;
-    return NK_OK;
+    return build_heavy(g, st);
 }
 
 }  // namespace
@@ -408,6 +411,7 @@ int build_csr_from_edges(nk_graph *g, int32_t n, int64_t m, const int32_t *d_u,
     NK_CUDA(cudaMemsetAsync(flags.p, 0, 2 * sizeof(int), st));
     if (m > 0) {
         k_count_deg<<<grid_for(m, 256), 256, 0, st>>>(d_u, d_v, m, n, deg.as<unsigned long long>(), d_bad);
+        ::nk::count_launch();
         NK_CUDA(cudaGetLastError());
     }
     int hbad = 0;
@@ -416,6 +420,7 @@ int build_csr_from_edges(nk_graph *g, int32_t n, int64_t m, const int32_t *d_u,
     if (hbad) return set_error(NK_ERR_GRAPH, "edge list holds a vertex id outside [0, %d)", n);
     // offsets of the raw (symmetrised, loop-free) buckets
     k_u64_to_i64<<<grid_for(n + 1, 256), 256, 0, st>>>(deg.as<unsigned long long>(), off.as<int64_t>(), n + 1);
+    ::nk::count_launch();
     NK_CUDA(cudaGetLastError());
     NK_TRY(scan_exclusive_i64(off.as<int64_t>(), off.as<int64_t>(), n + 1, nullptr, st));
     int64_t total = 0;
@@ -428,15 +433,19 @@ int build_csr_from_edges(nk_graph *g, int32_t n, int64_t m, const int32_t *d_u,
         // cursors: reuse deg as the running position of every bucket
         NK_CUDA(cudaMemcpyAsync(deg.p, off.p, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToDevice, st));
         k_scatter<<<grid_for(m, 256), 256, 0, st>>>(d_u, d_v, m, deg.as<unsigned long long>(), buf.as<int32_t>());
+        ::nk::count_launch();
         NK_CUDA(cudaGetLastError());
     }
     NK_TRY(ucnt.alloc(sizeof(int64_t) * (n + 1), st));
     NK_CUDA(cudaMemsetAsync(ucnt.p, 0, sizeof(int64_t) * (n + 1), st));
     k_sort_small<<<grid_for((int64_t)n * 32, 256), 256, 0, st>>>(off.as<int64_t>(), buf.as<int32_t>(), sorted.as<int32_t>(), ucnt.as<int64_t>(), n);
+    ::nk::count_launch();
     NK_CUDA(cudaGetLastError());
     k_sort_mid<<<std::max(1, std::min(n, 4 * num_sms())), 512, 0, st>>>(off.as<int64_t>(), buf.as<int32_t>(), sorted.as<int32_t>(), ucnt.as<int64_t>(), n);
+    ::nk::count_launch();
     NK_CUDA(cudaGetLastError());
     k_sort_big<<<std::max(1, std::min(n, 2 * num_sms())), 512, 0, st>>>(off.as<int64_t>(), buf.as<int32_t>(), sorted.as<int32_t>(), ucnt.as<int64_t>(), n);
+    ::nk::count_launch();
     NK_CUDA(cudaGetLastError());
     int64_t A = 0;
     Tmp tot;
@@ -448,8 +457,45 @@ int build_csr_from_edges(nk_graph *g, int32_t n, int64_t m, const int32_t *d_u,
     NK_TRY(g->rp.ensure(sizeof(int32_t) * (n + 1)));
     NK_TRY(g->col.ensure(sizeof(int32_t) * (A + 1)));
     k_compact_rows<<<grid_for((int64_t)(n + 1) * 32, 256), 256, 0, st>>>(off.as<int64_t>(), ucnt.as<int64_t>(), sorted.as<int32_t>(), g->rp.as<int32_t>(), g->col.as<int32_t>(), n, d_max);
+    ::nk::count_launch();
     NK_CUDA(cudaGetLastError());
     return finish_graph(g, st, d_max);
+}
+
+// Chunk table of the vertices whose degree exceeds kHeavyChunk, built once per graph on the
+// host from row_ptr: heavy vertex ids, the first chunk of each, and the owner of every
+// chunk.  Returns the number of chunks (0 for graphs without heavy vertices).
+int build_heavy(nk_graph *g, cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lk(g->heavy_mu);
+    if (g->heavy_H >= 0) return NK_OK;
+    std::vector<int32_t> rp(g->n + 1);
+    NK_CUDA(cudaMemcpyAsync(rp.data(), g->rp.p, sizeof(int32_t) * (g->n + 1), cudaMemcpyDeviceToHost, s));
+    NK_CUDA(cudaStreamSynchronize(s));
+    std::vector<int32_t> hv, hfirst, chunk_h;
+    int64_t c = 0;
+    for (int32_t v = 0; v < g->n; ++v) {
+        const int32_t deg = rp[v + 1] - rp[v];
+        if (deg <= kHeavyChunk) continue;
+        const int32_t nc = (deg + kHeavyChunk - 1) / kHeavyChunk;
+        hfirst.push_back((int32_t)c);
+        for (int32_t j = 0; j < nc; ++j) chunk_h.push_back((int32_t)hv.size());
+        hv.push_back(v);
+        c += nc;
+    }
+    hfirst.push_back((int32_t)c);
+    NK_TRY(g->heavy[0].ensure(sizeof(int32_t) * std::max<size_t>(hv.size(), 1)));
+    NK_TRY(g->heavy[1].ensure(sizeof(int32_t) * hfirst.size()));
+    NK_TRY(g->heavy[2].ensure(sizeof(int32_t) * std::max<size_t>(chunk_h.size(), 1)));
+    if (!hv.empty()) {
+        NK_CUDA(cudaMemcpyAsync(g->heavy[0].p, hv.data(), sizeof(int32_t) * hv.size(), cudaMemcpyHostToDevice, s));
+        NK_CUDA(cudaMemcpyAsync(g->heavy[2].p, chunk_h.data(), sizeof(int32_t) * chunk_h.size(), cudaMemcpyHostToDevice, s));
+    }
+    NK_CUDA(cudaMemcpyAsync(g->heavy[1].p, hfirst.data(), sizeof(int32_t) * hfirst.size(), cudaMemcpyHostToDevice, s));
+    NK_CUDA(cudaStreamSynchronize(s));
+    g->heavy_C = (int32_t)c;
+    g->heavy_H = (int32_t)hv.size();
+    return NK_OK;
 }
 
 }  // namespace nk
@@ -527,7 +573,9 @@ int nk_graph_from_csr(int32_t n, const int32_t *row_ptr, const int32_t *col, int
         if ((rc = fl.alloc(2 * sizeof(int), st)) != NK_OK) return fail(rc);
         if (cudaMemsetAsync(fl.p, 0, 2 * sizeof(int), st) != cudaSuccess) return fail(set_error(NK_ERR_CUDA, "memset"));
         k_check_ends<<<1, 1, 0, st>>>(drp.as<int32_t>(), n, n_arcs, fl.as<int>());
+        ::nk::count_launch();
         k_check_csr<<<grid_for((int64_t)n * 32, 256), 256, 0, st>>>(drp.as<int32_t>(), dcol.as<int32_t>(), n, n_arcs, false, fl.as<int>(), fl.as<int>() + 1);
+        ::nk::count_launch();
         int hb = 0;
         if (cudaMemcpyAsync(&hb, fl.p, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess)
@@ -535,6 +583,7 @@ int nk_graph_from_csr(int32_t n, const int32_t *row_ptr, const int32_t *col, int
         if (hb) return fail(set_error(NK_ERR_GRAPH, "row_ptr/col are not a CSR of %d vertices", n));
         if ((rc = du.alloc(sizeof(int32_t) * (n_arcs > 0 ? n_arcs : 1), st)) != NK_OK) return fail(rc);
         k_csr_rows<<<grid_for((int64_t)n * 32, 256), 256, 0, st>>>(drp.as<int32_t>(), n, du.as<int32_t>());
+        ::nk::count_launch();
         if ((rc = build_csr_from_edges(g, n, n_arcs, du.as<int32_t>(), dcol.as<int32_t>(), st)) != NK_OK)
             return fail(rc);
         *out = g;
@@ -552,7 +601,9 @@ int nk_graph_from_csr(int32_t n, const int32_t *row_ptr, const int32_t *col, int
     if ((rc = fl.alloc(2 * sizeof(int), st)) != NK_OK) return fail(rc);
     if (cudaMemsetAsync(fl.p, 0, 2 * sizeof(int), st) != cudaSuccess) return fail(set_error(NK_ERR_CUDA, "memset"));
     k_check_ends<<<1, 1, 0, st>>>(g->rp.as<int32_t>(), n, n_arcs, fl.as<int>());
+    ::nk::count_launch();
     k_check_csr<<<grid_for((int64_t)n * 32, 256), 256, 0, st>>>(g->rp.as<int32_t>(), g->col.as<int32_t>(), n, n_arcs, (flags & NK_CSR_VALIDATE) != 0, fl.as<int>(), fl.as<int>() + 1);
+    ::nk::count_launch();
     int h[2] = {0, 0};
     if (cudaMemcpyAsync(h, fl.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
@@ -561,6 +612,7 @@ int nk_graph_from_csr(int32_t n, const int32_t *row_ptr, const int32_t *col, int
     if (h[0] & 2) return fail(set_error(NK_ERR_GRAPH, "a row is unsorted, has a duplicate or a self-loop"));
     if (h[0] & 4) return fail(set_error(NK_ERR_GRAPH, "adjacency is not symmetric"));
     g->max_deg = h[1];
+    if ((rc = build_heavy(g, st)) != NK_OK) return fail(rc);
     *out = g;
     return NK_OK;
 }
@@ -586,6 +638,7 @@ int nk_graph_generate(int kind, const double *params, int32_t n_or_scale, uint64
             NK_TRY(eu.alloc(sizeof(int32_t) * m, st));
             NK_TRY(ev.alloc(sizeof(int32_t) * m, st));
             k_er_all_pairs<<<grid_for(m, 256), 256, 0, st>>>(N, eu.as<int32_t>(), ev.as<int32_t>());
+            ::nk::count_launch();
             NK_CUDA(cudaGetLastError());
         } else if (N > 0 && p > 0.0) {
             const int64_t chunks = (int64_t)((N + kErChunk - 1) / kErChunk);
@@ -593,6 +646,7 @@ int nk_graph_generate(int kind, const double *params, int32_t n_or_scale, uint64
             NK_TRY(cnt.alloc(sizeof(int64_t) * chunks, st));
             NK_TRY(tot.alloc(sizeof(int64_t), st));
             k_er<<<grid_for(chunks, 128), 128, 0, st>>>(N, p, seed, cnt.as<int64_t>(), nullptr, nullptr, nullptr);
+            ::nk::count_launch();
             NK_CUDA(cudaGetLastError());
             NK_TRY(scan_exclusive_i64(cnt.as<int64_t>(), cnt.as<int64_t>(), chunks, tot.as<int64_t>(), st));
             NK_CUDA(cudaMemcpyAsync(&m, tot.p, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -600,6 +654,7 @@ int nk_graph_generate(int kind, const double *params, int32_t n_or_scale, uint64
             NK_TRY(eu.alloc(sizeof(int32_t) * (m + 1), st));
             NK_TRY(ev.alloc(sizeof(int32_t) * (m + 1), st));
             k_er<<<grid_for(chunks, 128), 128, 0, st>>>(N, p, seed, nullptr, cnt.as<int64_t>(), eu.as<int32_t>(), ev.as<int32_t>());
+            ::nk::count_launch();
             NK_CUDA(cudaGetLastError());
         }
     } else if (kind == NK_GEN_BA) {
@@ -612,6 +667,7 @@ int nk_graph_generate(int kind, const double *params, int32_t n_or_scale, uint64
         NK_TRY(eu.alloc(sizeof(int32_t) * m, st));
         NK_TRY(ev.alloc(sizeof(int32_t) * m, st));
         k_ba<<<grid_for(m, 256), 256, 0, st>>>(m, m0, seed, eu.as<int32_t>(), ev.as<int32_t>());
+        ::nk::count_launch();
         NK_CUDA(cudaGetLastError());
     } else if (kind == NK_GEN_RMAT) {
         const int scale = n_or_scale;
@@ -629,6 +685,7 @@ int nk_graph_generate(int kind, const double *params, int32_t n_or_scale, uint64
         NK_TRY(eu.alloc(sizeof(int32_t) * m, st));
         NK_TRY(ev.alloc(sizeof(int32_t) * m, st));
         k_rmat<<<grid_for(m, 256), 256, 0, st>>>(m, scale, seed, t1, t2, t3, eu.as<int32_t>(), ev.as<int32_t>());
+        ::nk::count_launch();
         NK_CUDA(cudaGetLastError());
     } else {
         return set_error(NK_ERR_ARG, "unknown generator kind %d", kind);

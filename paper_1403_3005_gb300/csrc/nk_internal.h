@@ -30,6 +30,11 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
         if (nk_rc_ != NK_OK) return nk_rc_; \
     } while (0)
 
+// ---------------------------------------------------------------- launch accounting
+// Every kernel launch of the library bumps this process-wide counter.
+extern std::atomic<uint64_t> g_launches;
+inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
 // ---------------------------------------------------------------- stream / limits
 cudaStream_t stream();
 uint64_t wait_limit_ns();
@@ -97,6 +102,10 @@ struct nk_graph {
     nk::DevBuf ws[8];
     nk::Tuned tuned;
     std::atomic<int64_t> pending{0};  // serving requests referencing this graph
+    // chunk table of high-degree vertices for the batched form (built on first use)
+    std::mutex heavy_mu;
+    nk::DevBuf heavy[3];
+    int32_t heavy_H = -1, heavy_C = 0;
 };
 
 namespace nk {
@@ -106,6 +115,14 @@ namespace nk {
 // null) receives the sum.  Stream-ordered on st.
 int scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t count, int64_t *total,
                        cudaStream_t st);
+
+// ---------------------------------------------------------------- high-degree vertices
+// Rows longer than kHeavyChunk arcs are processed as chunks of kHeavyChunk arcs by
+// different warps (partial sums reduced in chunk order), so that one hub does not keep
+// one warp busy while the rest of the GPU waits at the next level barrier.
+constexpr int kHeavyChunk = 256;
+// Builds g->heavy (vertex ids, first chunk per vertex, owner per chunk) once per graph.
+int build_heavy(nk_graph *g, cudaStream_t s);
 
 // ---------------------------------------------------------------- CSR build (nk_graph.cu)
 // Canonical CSR of the undirected edge list (u[i], v[i]) (device arrays), written into

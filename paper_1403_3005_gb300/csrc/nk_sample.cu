@@ -110,18 +110,23 @@ int sample_sources_device(int32_t n, uint64_t seed, int32_t k, int32_t *d_src, c
     SelState *S = state.as<SelState>();
     unsigned *H = hist.as<unsigned>();
     k_sel_init<<<1, 256, 0, st>>>(S, k, H);
+    ::nk::count_launch();
     NK_CUDA(cudaGetLastError());
     int blocks = (int)std::min<int64_t>(((int64_t)n + 255) / 256, 4LL * num_sms());
     for (int pass = 0; pass < 8; ++pass) {
         const int shift = 56 - 8 * pass;
         k_sel_hist<<<blocks, 256, 0, st>>>(n, seed, S, shift, H);
+        ::nk::count_launch();
         k_sel_digit<<<1, 32, 0, st>>>(S, shift, H);
+        ::nk::count_launch();
     }
     NK_CUDA(cudaGetLastError());
     k_sel_count<<<(unsigned)ntiles, kTileV, 0, st>>>(n, seed, S, tiles.as<int64_t>());
+    ::nk::count_launch();
     NK_CUDA(cudaGetLastError());
     NK_TRY(scan_exclusive_i64(tiles.as<int64_t>(), tiles.as<int64_t>(), ntiles, nullptr, st));
     k_sel_write<<<(unsigned)ntiles, kTileV, 0, st>>>(n, seed, S, tiles.as<int64_t>(), d_src);
+    ::nk::count_launch();
     NK_CUDA(cudaGetLastError());
     return NK_OK;
 }

@@ -56,6 +56,10 @@ struct SrcArgs {
     double alpha;
     int dir;
     int forward_only;
+    // rows longer than kHeavyChunk: chunk table and per-chunk partial sums
+    const int32_t *hv, *hfirst, *chunk_h;
+    int32_t H, C;
+    unsigned long long *part;
 };
 
 template <int TPV> struct Lanes {
@@ -73,6 +77,43 @@ template <int TPV> struct Lanes {
 
 __device__ __forceinline__ int degree(const int32_t *rp, int v) { return __ldg(rp + v + 1) - __ldg(rp + v); }
 
+__device__ __forceinline__ bool heavy(const SrcArgs &a, int v) { return degree(a.rp, v) > kHeavyChunk; }
+
+// Chunk c of a heavy vertex: its vertex h and arc range [j0, j1).
+__device__ __forceinline__ void chunk_of(const SrcArgs &a, long long c, int &h, int &j0, int &j1)
+{
+    const int i = __ldg(a.chunk_h + c);
+    h = __ldg(a.hv + i);
+    j0 = __ldg(a.rp + h) + (int)(c - __ldg(a.hfirst + i)) * kHeavyChunk;
+    j1 = min(j0 + kHeavyChunk, __ldg(a.rp + h + 1));
+}
+
+// One arc (v, w) of a top-down step from level d: claim w for level d+1 (queued once,
+// warp-aggregated), and add sigma[v] if w is at level d+1.
+__device__ __forceinline__ void td_arc(const SrcArgs &a, int d, int w, unsigned long long sv,
+                                       int qnext, unsigned long long *s_mf, bool &ovf)
+{
+    int dw = dev::ldcg(a.dist + w);
+    bool claim = false;
+    if (dw < 0) {
+        const int old = atomicCAS(a.dist + w, -1, d + 1);
+        claim = old < 0;
+        dw = claim ? d + 1 : old;
+    }
+    if (dw == d + 1) {
+        const unsigned long long old = atomicAdd(a.sp + w, sv);
+        ovf |= old + sv < old;
+    }
+    if (claim) {
+        cg::coalesced_group g = cg::coalesced_threads();
+        int pos = 0;
+        if (g.thread_rank() == 0) pos = atomicAdd(a.cnt + d + 1, (int)g.size());
+        pos = g.shfl(pos, 0) + (int)g.thread_rank();
+        a.queue[qnext + pos] = w;
+        atomicAdd(s_mf, (unsigned long long)degree(a.rp, w));
+    }
+}
+
 // ------------------------------------------------------------------ top-down level d
 template <int TPV>
 __device__ void td_level(const SrcArgs &a, int d, int qo, int nf, int qnext,
@@ -88,31 +129,18 @@ __device__ void td_level(const SrcArgs &a, int d, int qo, int nf, int qnext,
             if (qo >= 0) v = dev::ldcg(a.queue + qo + item);
             else if (dev::ldcg(a.dist + item) == d) v = (int)item;
         }
-        if (v < 0) continue;
+        if (v < 0 || heavy(a, v)) continue;
         const unsigned long long sv = dev::ldcg(a.sp + v);
         const int beg = __ldg(a.rp + v), end = __ldg(a.rp + v + 1);
-        for (int j = beg + L.lg; j < end; j += TPV) {
-            const int w = __ldg(a.col + j);
-            int dw = dev::ldcg(a.dist + w);
-            bool claim = false;
-            if (dw < 0) {
-                const int old = atomicCAS(a.dist + w, -1, d + 1);
-                claim = old < 0;
-                dw = claim ? d + 1 : old;
-            }
-            if (dw == d + 1) {
-                const unsigned long long old = atomicAdd(a.sp + w, sv);
-                ovf |= old + sv < old;
-            }
-            if (claim) {
-                cg::coalesced_group g = cg::coalesced_threads();
-                int pos = 0;
-                if (g.thread_rank() == 0) pos = atomicAdd(a.cnt + d + 1, (int)g.size());
-                pos = g.shfl(pos, 0) + (int)g.thread_rank();
-                a.queue[qnext + pos] = w;
-                atomicAdd(s_mf, (unsigned long long)degree(a.rp, w));
-            }
-        }
+        for (int j = beg + L.lg; j < end; j += TPV) td_arc(a, d, __ldg(a.col + j), sv, qnext, s_mf, ovf);
+    }
+    // heavy frontier vertices: one warp per chunk of kHeavyChunk arcs
+    for (long long c = L.wid; c < a.C; c += L.nw) {
+        int h, j0, j1;
+        chunk_of(a, c, h, j0, j1);
+        if (dev::ldcg(a.dist + h) != d) continue;
+        const unsigned long long sv = dev::ldcg(a.sp + h);
+        for (int j = j0 + L.lane; j < j1; j += 32) td_arc(a, d, __ldg(a.col + j), sv, qnext, s_mf, ovf);
     }
 }
 
@@ -124,7 +152,7 @@ __device__ void bu_level(const SrcArgs &a, int d, int *s_cnt, unsigned long long
     const Lanes<TPV> L;
     for (long long base = L.wid * G; base < a.n; base += L.nw * G) {
         const long long w = base + L.gw;
-        const bool act = w < a.n && dev::ldcg(a.dist + w) < 0;
+        const bool act = w < a.n && dev::ldcg(a.dist + w) < 0 && !heavy(a, (int)w);
         unsigned long long acc = 0;
         int beg = 0, end = 0;
         if (act) {
@@ -148,6 +176,45 @@ __device__ void bu_level(const SrcArgs &a, int d, int *s_cnt, unsigned long long
             atomicAdd(s_mf, (unsigned long long)(end - beg));
         }
     }
+    // heavy unvisited vertices: per-chunk partial sums (finished by bu_heavy_finish)
+    for (long long c = L.wid; c < a.C; c += L.nw) {
+        int h, j0, j1;
+        chunk_of(a, c, h, j0, j1);
+        if (dev::ldcg(a.dist + h) >= 0) continue;
+        unsigned long long acc = 0;
+        for (int j = j0 + L.lane; j < j1; j += 32) {
+            const int v = __ldg(a.col + j);
+            if (dev::ldcg(a.dist + v) == d) {
+                const unsigned long long y = acc + dev::ldcg(a.sp + v);
+                ovf |= y < acc;
+                acc = y;
+            }
+        }
+        acc = dev::group_sum_u64<32>(acc, ovf);
+        if (L.lane == 0) a.part[c] = acc;
+    }
+}
+
+// After a barrier: heavy unvisited vertices add their chunk sums in chunk order.
+__device__ void bu_heavy_finish(const SrcArgs &a, int d, int *s_cnt, unsigned long long *s_mf, bool &ovf)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.H;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int h = __ldg(a.hv + i);
+        if (dev::ldcg(a.dist + h) >= 0) continue;
+        unsigned long long acc = 0;
+        for (int c = __ldg(a.hfirst + i); c < __ldg(a.hfirst + i + 1); ++c) {
+            const unsigned long long y = acc + dev::ldcg(a.part + c);
+            ovf |= y < acc;
+            acc = y;
+        }
+        if (acc != 0) {
+            a.dist[h] = d + 1;
+            a.sp[h] = acc;
+            atomicAdd(s_cnt, 1);
+            atomicAdd(s_mf, (unsigned long long)degree(a.rp, h));
+        }
+    }
 }
 
 // ------------------------------------------------------------------ backward level d
@@ -163,6 +230,7 @@ __device__ void back_level(const SrcArgs &a, int d, int qo, int nd)
         if (item < count) {
             if (qo >= 0) v = dev::ldcg(a.queue + qo + item);
             else if (dev::ldcg(a.dist + item) == d) v = (int)item;
+            if (v >= 0 && heavy(a, v)) v = -1;
         }
         double acc = 0.0;
         if (v >= 0) {
@@ -179,6 +247,36 @@ __device__ void back_level(const SrcArgs &a, int d, int qo, int nd)
             a.sp[v] = (unsigned long long)__double_as_longlong(__ddiv_rn(__dadd_rn(1.0, delta), sv));
             if (delta != 0.0) a.scores[v] += delta;
         }
+    }
+    // heavy vertices of level d: per-chunk partial sums of psi
+    for (long long c = L.wid; c < a.C; c += L.nw) {
+        int h, j0, j1;
+        chunk_of(a, c, h, j0, j1);
+        if (dev::ldcg(a.dist + h) != d) continue;
+        double acc = 0.0;
+        for (int j = j0 + L.lane; j < j1; j += 32) {
+            const int w = __ldg(a.col + j);
+            if (dev::ldcg(a.dist + w) == d + 1) acc += __longlong_as_double((long long)dev::ldcg(a.sp + w));
+        }
+        acc = dev::group_sum<32>(acc);
+        if (L.lane == 0) a.part[c] = (unsigned long long)__double_as_longlong(acc);
+    }
+}
+
+// After a barrier: heavy vertices of level d add their chunk sums in chunk order.
+__device__ void back_heavy_finish(const SrcArgs &a, int d)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.H;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int h = __ldg(a.hv + i);
+        if (dev::ldcg(a.dist + h) != d) continue;
+        double acc = 0.0;
+        for (int c = __ldg(a.hfirst + i); c < __ldg(a.hfirst + i + 1); ++c)
+            acc += __longlong_as_double((long long)dev::ldcg(a.part + c));
+        const double sv = __ull2double_rn(dev::ldcg(a.sp + h));
+        const double delta = __dmul_rn(sv, acc);
+        a.sp[h] = (unsigned long long)__double_as_longlong(__ddiv_rn(__dadd_rn(1.0, delta), sv));
+        if (delta != 0.0) a.scores[h] += delta;
     }
 }
 
@@ -218,8 +316,15 @@ __global__ void __launch_bounds__(kThreads) k_source(SrcArgs a)
         __syncthreads();
         const bool use_bu = a.dir == NK_DIR_BOTTOM_UP ||
                             (a.dir == NK_DIR_AUTO && a.alpha * (double)mf > (double)mu);
-        if (use_bu) bu_level<TPV>(a, d, &s_cnt, &s_mf, ovf);
-        else td_level<TPV>(a, d, qo, nf, qtail, &s_mf, ovf);
+        if (use_bu) {
+            bu_level<TPV>(a, d, &s_cnt, &s_mf, ovf);
+            if (a.H > 0) {
+                if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+                bu_heavy_finish(a, d, &s_cnt, &s_mf, ovf);
+            }
+        } else {
+            td_level<TPV>(a, d, qo, nf, qtail, &s_mf, ovf);
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             if (s_cnt) atomicAdd(a.cnt + d + 1, s_cnt);
@@ -254,6 +359,10 @@ __global__ void __launch_bounds__(kThreads) k_source(SrcArgs a)
     for (int l = D; l >= 1; --l) {
         back_level<TPV>(a, l, dev::ldcg(a.qoff + l), dev::ldcg(a.cnt + l));
         if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+        if (a.H > 0) {
+            back_heavy_finish(a, l);
+            if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+        }
     }
 }
 
@@ -303,7 +412,7 @@ int auto_tpv(const nk_graph *g)
 }
 
 // workspace slots in nk_graph::ws used by this form
-enum { WS_DIST = 0, WS_SP = 1, WS_QUEUE = 2, WS_LEVELS = 3, WS_CTRL = 4 };
+enum { WS_DIST = 0, WS_SP = 1, WS_QUEUE = 2, WS_LEVELS = 3, WS_CTRL = 4, WS_PART = 7 };
 
 int run(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores, const RunCfg &cfg,
         RunStats *st, cudaStream_t s, bool forward_only, int32_t *d_dist_out,
@@ -317,6 +426,8 @@ int run(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores, const Ru
     const size_t lv = (size_t)n + 3;
     NK_TRY(ws[WS_LEVELS].ensure(lv * (sizeof(int32_t) * 2 + sizeof(long long))));
     NK_TRY(ws[WS_CTRL].ensure(sizeof(Ctrl)));
+    NK_TRY(build_heavy(g, s));
+    NK_TRY(ws[WS_PART].ensure(sizeof(unsigned long long) * std::max<int64_t>(g->heavy_C, 1)));
     const int tpv = cfg.tpv > 0 ? cfg.tpv : auto_tpv(g);
     Launch L;
     NK_TRY(pick_launch(tpv, L));
@@ -339,6 +450,12 @@ int run(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores, const Ru
     a.alpha = cfg.alpha > 0 ? cfg.alpha : 1.0;
     a.dir = cfg.direction;
     a.forward_only = forward_only ? 1 : 0;
+    a.hv = g->heavy[0].as<int32_t>();
+    a.hfirst = g->heavy[1].as<int32_t>();
+    a.chunk_h = g->heavy[2].as<int32_t>();
+    a.H = g->heavy_H;
+    a.C = g->heavy_C;
+    a.part = ws[WS_PART].as<unsigned long long>();
     NK_CUDA(cudaMemsetAsync(a.ctrl, 0, sizeof(Ctrl), s));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cfg.time_kernels) {
@@ -350,6 +467,7 @@ int run(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores, const Ru
         a.src = d_src + i;
         void *args[] = {&a};
         NK_CUDA(cudaLaunchCooperativeKernel(L.fn, dim3(std::max(1, L.grid / std::max(1, cfg.grid_div))), dim3(kThreads), args, 0, s));
+        ::nk::count_launch();
     }
     if (cfg.time_kernels) NK_CUDA(cudaEventRecord(e1, s));
     Ctrl h;

@@ -100,6 +100,7 @@ SIGNATURES = {
     "nk_set_stream": (_INT, [_P]),
     "nk_set_wait_limit_ns": (_INT, [_U64]),
     "nk_selftest_wait_timeout": (_INT, [_U64]),
+    "nk_launch_count": (_U64, []),
     "nk_last_error": (ctypes.c_char_p, []),
     "nk_version": (ctypes.c_char_p, []),
 }
@@ -261,10 +262,19 @@ def run_opts(mode=MODE_AUTO, batch=0, tpv=0, direction=DIR_AUTO, alpha=0.0, flag
 
 
 def _out_scores(g: Graph, out, opts: RunOpts | None):
+    """Output buffer: a CUDA tensor (device pointer), a float64 numpy array (host,
+    e.g. a view of pinned memory) or None (a new host array)."""
     if out is not None and _is_torch(out):
-        o = opts if opts is not None else run_opts()
+        o = run_opts() if opts is None else RunOpts.from_buffer_copy(opts)
         o.flags |= RUN_DEVICE_PTRS
         return _dev_ptr(out), o, out
+    if opts is not None and (opts.flags & RUN_DEVICE_PTRS):
+        opts = RunOpts.from_buffer_copy(opts)
+        opts.flags &= ~RUN_DEVICE_PTRS
+    if out is not None:
+        if out.dtype != np.float64 or not out.flags.c_contiguous or len(out) != g.n:
+            raise ValueError("host output must be a contiguous float64 array of n entries")
+        return _np_ptr(out), opts, out
     arr = np.empty(g.n, np.float64)
     return _np_ptr(arr), opts, arr
 
@@ -375,6 +385,10 @@ def set_wait_limit_ns(ns: int) -> None:
 
 def selftest_wait_timeout(limit_ns: int) -> int:
     return lib().nk_selftest_wait_timeout(limit_ns)
+
+
+def launch_count() -> int:
+    return int(lib().nk_launch_count())
 
 
 def last_error() -> str:

@@ -110,3 +110,17 @@ def relabel(graph, seed):
     n, u, v = graph
     perm = np.random.default_rng(seed).permutation(n).astype(np.int32)
     return n, perm[u], perm[v]
+
+
+def with_hubs(graph, degrees, seed):
+    """The graph plus one hub per entry of `degrees`: hub i (vertex i) gets edges to
+    degrees[i] distinct other vertices chosen at random (so rows cross the 256-arc chunk
+    boundary of the GPU kernels when asked to)."""
+    n, u, v = graph
+    rng = np.random.default_rng(seed)
+    us, vs = [u], [v]
+    for h, d in enumerate(degrees):
+        others = rng.choice(np.setdiff1d(np.arange(n), [h]), size=d, replace=False)
+        us.append(np.full(d, h, np.int64))
+        vs.append(others)
+    return n, np.concatenate(us).astype(np.int32), np.concatenate(vs).astype(np.int32)

@@ -54,6 +54,10 @@ SMALL = {
     "hypercube": G.hypercube(6), "tree": G.random_tree(300, 3), "gnp": G.gnp(200, 0.04, 5),
     "components": G.disjoint_union(G.path(7), G.gnp(60, 0.1, 2), G.star(5), G.complete(1)),
     "isolated": G.disjoint_union(G.complete(1), G.complete(1), G.path(3)),
+    "star_big": G.star(1500),
+    "hubs": G.with_hubs(G.disjoint_union(*[G.complete(1)] * 5, G.gnp(1200, 0.004, 9)),
+                        [256, 257, 512, 513, 1000], 4),
+    "hub_path": G.with_hubs(G.path(700), [600, 300], 5),
 }
 
 
