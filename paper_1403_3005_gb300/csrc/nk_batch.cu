@@ -46,6 +46,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kErrDepth = 100;  // internal status: BFS deeper than the level slabs
+constexpr int kStartLevels = 48; // level slabs of a first attempt
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kChunk = kHeavyChunk;  // arcs per work item; longer rows are split
 
@@ -690,98 +691,114 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
     constexpr int B = 64 * W;
     NK_TRY(build_heavy(g, s));
     DevBuf *ws = scratch(cfg, g);
-    const int lcap = cfg.lcap > 0 ? std::min(cfg.lcap, std::max(g->n, 4)) : choose_lcap(g, B, ws);
-    if (lcap < 4) return set_error(NK_ERR_NOMEM, "not enough device memory for a batch of %d sources", B);
-    const Layout L = layout(g, B, lcap);
-    NK_TRY(ws[WS_BATCH].ensure(L.total));
+    // level slabs: start small; batches whose BFS is deeper are rerun once with the
+    // largest cap that free memory allows, then (if still deeper) by the per-source form
+    const int lmax = cfg.lcap > 0 ? std::min(cfg.lcap, std::max(g->n, 4)) : choose_lcap(g, B, ws);
+    if (lmax < 4) return set_error(NK_ERR_NOMEM, "not enough device memory for a batch of %d sources", B);
+    const int lstart = cfg.lcap > 0 ? lmax : std::min(lmax, std::max(kStartLevels, 4));
     const int nb = (k + B - 1) / B;
     NK_TRY(ws[WS_BCTRL].ensure(sizeof(Ctrl) * nb));
     const int bps = blocks_per_sm<W>();
     if (bps < 1) return set_error(NK_ERR_CUDA, "batched kernel cannot be resident");
-    char *base = ws[WS_BATCH].as<char>();
-    BArgs a;
-    a.n = g->n;
-    a.A = g->A;
-    a.rp = g->rp.as<int32_t>();
-    a.col = g->col.as<int32_t>();
-    a.lcap = lcap;
-    a.F = reinterpret_cast<unsigned long long *>(base + L.off_F);
-    a.vis = reinterpret_cast<unsigned long long *>(base + L.off_vis);
-    a.sp = reinterpret_cast<unsigned long long *>(base + L.off_sp);
-    a.qmark = reinterpret_cast<int32_t *>(base + L.off_qmark);
-    a.queue = reinterpret_cast<int32_t *>(base + L.off_queue);
-    a.qcap = L.qcap;
-    const size_t lv = (size_t)lcap + 3;
-    char *cb = base + L.off_cnt;
-    a.mfv = reinterpret_cast<unsigned long long *>(cb);
-    a.dmu = a.mfv + lv;
-    a.vcnt = reinterpret_cast<int32_t *>(a.dmu + lv);
-    a.qcnt = a.vcnt + lv;
-    a.qoff = a.qcnt + lv;
-    a.scores = d_scores;
-    a.hv = g->heavy[0].as<int32_t>();
-    a.hfirst = g->heavy[1].as<int32_t>();
-    a.chunk_h = g->heavy[2].as<int32_t>();
-    a.H = g->heavy_H;
-    a.C = g->heavy_C;
-    a.part = reinterpret_cast<unsigned long long *>(base + L.off_part);
-    a.limit_ns = cfg.limit_ns ? cfg.limit_ns : wait_limit_ns();
-    a.alpha = cfg.alpha > 0 ? cfg.alpha : 1.0;
-    a.dir = cfg.direction;
-    Ctrl *ctrls = ws[WS_BCTRL].as<Ctrl>();
-    NK_CUDA(cudaMemsetAsync(ctrls, 0, sizeof(Ctrl) * nb, s));
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (cfg.time_kernels) {
-        NK_CUDA(cudaEventCreate(&e0));
-        NK_CUDA(cudaEventCreate(&e1));
-        NK_CUDA(cudaEventRecord(e0, s));
-    }
     const int grid = std::max(1, bps * num_sms() / std::max(1, cfg.grid_div));
-    for (int bi = 0; bi < nb; ++bi) {
-        a.src = d_src + (size_t)bi * B;
-        a.nsrc = std::min(B, k - bi * B);
-        a.ctrl = ctrls + bi;
-        void *args[] = {&a};
-        NK_CUDA(cudaLaunchCooperativeKernel((const void *)k_batch<W>, dim3(grid), dim3(kThreads), args, 0, s));
-        ::nk::count_launch();
-    }
-    if (cfg.time_kernels) NK_CUDA(cudaEventRecord(e1, s));
-    std::vector<Ctrl> h(nb);
-    NK_CUDA(cudaMemcpyAsync(h.data(), ctrls, sizeof(Ctrl) * nb, cudaMemcpyDeviceToHost, s));
-    NK_CUDA(cudaStreamSynchronize(s));
-    if (st) {
-        st->mode = NK_MODE_BATCHED;
-        st->batch = B;
-        st->tpv = 32;
-        st->launches += nb;
-        st->alpha = a.alpha;
-        for (const Ctrl &c : h) {
-            st->max_depth = std::max(st->max_depth, c.depth);
-            st->td_levels += c.td_levels;
-            st->bu_levels += c.bu_levels;
-        }
+    Ctrl *ctrls = ws[WS_BCTRL].as<Ctrl>();
+    std::vector<int> todo(nb);
+    for (int bi = 0; bi < nb; ++bi) todo[bi] = bi;
+    double alpha_used = cfg.alpha > 0 ? cfg.alpha : 1.0;
+    for (int lcap = lstart;;) {
+        const Layout L = layout(g, B, lcap);
+        NK_TRY(ws[WS_BATCH].ensure(L.total));
+        char *base = ws[WS_BATCH].as<char>();
+        BArgs a;
+        a.n = g->n;
+        a.A = g->A;
+        a.rp = g->rp.as<int32_t>();
+        a.col = g->col.as<int32_t>();
+        a.lcap = lcap;
+        a.F = reinterpret_cast<unsigned long long *>(base + L.off_F);
+        a.vis = reinterpret_cast<unsigned long long *>(base + L.off_vis);
+        a.sp = reinterpret_cast<unsigned long long *>(base + L.off_sp);
+        a.qmark = reinterpret_cast<int32_t *>(base + L.off_qmark);
+        a.queue = reinterpret_cast<int32_t *>(base + L.off_queue);
+        a.qcap = L.qcap;
+        const size_t lv = (size_t)lcap + 3;
+        char *cb = base + L.off_cnt;
+        a.mfv = reinterpret_cast<unsigned long long *>(cb);
+        a.dmu = a.mfv + lv;
+        a.vcnt = reinterpret_cast<int32_t *>(a.dmu + lv);
+        a.qcnt = a.vcnt + lv;
+        a.qoff = a.qcnt + lv;
+        a.scores = d_scores;
+        a.hv = g->heavy[0].as<int32_t>();
+        a.hfirst = g->heavy[1].as<int32_t>();
+        a.chunk_h = g->heavy[2].as<int32_t>();
+        a.H = g->heavy_H;
+        a.C = g->heavy_C;
+        a.part = reinterpret_cast<unsigned long long *>(base + L.off_part);
+        a.limit_ns = cfg.limit_ns ? cfg.limit_ns : wait_limit_ns();
+        a.alpha = alpha_used;
+        a.dir = cfg.direction;
+        NK_CUDA(cudaMemsetAsync(ctrls, 0, sizeof(Ctrl) * nb, s));
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (cfg.time_kernels) {
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            st->kernel_ms += ms;
+            NK_CUDA(cudaEventCreate(&e0));
+            NK_CUDA(cudaEventCreate(&e1));
+            NK_CUDA(cudaEventRecord(e0, s));
         }
+        for (int bi : todo) {
+            a.src = d_src + (size_t)bi * B;
+            a.nsrc = std::min(B, k - bi * B);
+            a.ctrl = ctrls + bi;
+            void *args[] = {&a};
+            NK_CUDA(cudaLaunchCooperativeKernel((const void *)k_batch<W>, dim3(grid), dim3(kThreads), args, 0, s));
+            ::nk::count_launch();
+        }
+        if (cfg.time_kernels) NK_CUDA(cudaEventRecord(e1, s));
+        std::vector<Ctrl> h(nb);
+        NK_CUDA(cudaMemcpyAsync(h.data(), ctrls, sizeof(Ctrl) * nb, cudaMemcpyDeviceToHost, s));
+        NK_CUDA(cudaStreamSynchronize(s));
+        if (st) {
+            st->mode = NK_MODE_BATCHED;
+            st->batch = B;
+            st->tpv = 32;
+            st->launches += (int64_t)todo.size();
+            st->alpha = alpha_used;
+            for (int bi : todo) {
+                st->max_depth = std::max(st->max_depth, h[bi].depth);
+                st->td_levels += h[bi].td_levels;
+                st->bu_levels += h[bi].bu_levels;
+            }
+            if (cfg.time_kernels) {
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                st->kernel_ms += ms;
+            }
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        bool ovf = false;
+        std::vector<int> deep;
+        for (int bi : todo) {
+            if (h[bi].err == NK_ERR_TIMEOUT)
+                return set_error(NK_ERR_TIMEOUT, "batched sweep aborted: a bounded grid wait ran out");
+            ovf |= h[bi].ovf != 0;
+            if (h[bi].err == kErrDepth) deep.push_back(bi);
+        }
+        if (ovf) return set_error(NK_ERR_OVERFLOW, "a shortest-path count exceeded 2^64 - 1");
+        if (deep.empty()) return NK_OK;
+        if (lcap < lmax) {
+            todo = deep;
+            lcap = lmax;
+            continue;
+        }
+        // deeper than any level cap that fits: the per-source form takes these sources
+        for (int bi : deep) {
+            RunCfg pc = cfg;
+            pc.tpv = 0;
+            NK_TRY(run_per_source(g, d_src + (size_t)bi * B, std::min(B, k - bi * B), d_scores, pc, st, s));
+        }
+        return NK_OK;
     }
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    bool ovf = false;
-    for (int bi = 0; bi < nb; ++bi) {
-        if (h[bi].err == NK_ERR_TIMEOUT) return set_error(NK_ERR_TIMEOUT, "batched sweep aborted: a bounded grid wait ran out");
-        ovf |= h[bi].ovf != 0;
-    }
-    if (ovf) return set_error(NK_ERR_OVERFLOW, "a shortest-path count exceeded 2^64 - 1");
-    // batches deeper than the level slabs: their sources go through the per-source form
-    for (int bi = 0; bi < nb; ++bi) {
-        if (h[bi].err != kErrDepth) continue;
-        RunCfg pc = cfg;
-        pc.tpv = 0;
-        NK_TRY(run_per_source(g, d_src + (size_t)bi * B, std::min(B, k - bi * B), d_scores, pc, st, s));
-    }
-    return NK_OK;
 }
 
 }  // namespace
