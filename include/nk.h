@@ -106,6 +106,29 @@ int nk_sample_sources(int32_t n, uint64_t seed, int32_t k, int32_t *src, uint32_
  * sigma exceeds 2^64 - 1 (outputs are then unspecified). */
 int nk_sssp(const nk_graph *g, int32_t s, int32_t *dist, uint64_t *sigma);
 
+/* Allocation-free forward sweep.  No counterpart in the paper: it is a service for
+ * callers that cannot allocate device memory when they call in - code running under an
+ * allocator that forbids cudaMalloc/cudaFree, or a host library that must not grow its
+ * device footprint after start-up.  Same results as nk_sssp (dist[n], sigma[n]) on a
+ * canonical CSR the caller already holds on the device:
+ *   row_ptr[n+1], col[n_arcs]  device pointers to a canonical CSR (as nk_graph_export_csr
+ *                              writes it; not re-validated), read only;
+ *   dist[n] (int32), sigma[n] (uint64)  device output buffers owned by the caller;
+ *   stream                      cudaStream_t the work is ordered on (NULL = default);
+ *                              the call returns after the results are written.
+ * Scratch (control words, BFS queue, per-level counters) is one static device array of
+ * about 20 MiB that every GPU loading the library holds until the process exits, so
+ * 1 <= n <= 1048576 (2^20); a larger n returns NK_ERR_ARG with a message.  The call makes
+ * no cudaMalloc, cudaFree or other allocating call.  The first call on a device looks up
+ * that device's address of the array (cudaGetSymbolAddress) with the device current:
+ * make that first call before any stream capture.  All calls share the one array, so
+ * calls that overlap on the GPU race: serialise them (one stream, or host ordering).
+ * Rows are not split into chunks here, so hubs make it slower than nk_sssp.
+ * Errors: NK_ERR_ARG, NK_ERR_OVERFLOW (sigma exceeded 2^64 - 1), NK_ERR_TIMEOUT,
+ * NK_ERR_CUDA. */
+int nk_sssp_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col, int64_t n_arcs,
+                    int32_t s, int32_t *dist, uint64_t *sigma, void *stream);
+
 /* ---------------------------------------------------------------- betweenness */
 #define NK_MODE_AUTO 0       /* batched where it fits, per-source otherwise */
 #define NK_MODE_PER_SOURCE 1 /* plain per-source kernel (one BFS tree at a time) */

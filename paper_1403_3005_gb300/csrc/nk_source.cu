@@ -28,6 +28,8 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <climits>
+#include <mutex>
 
 #include "nk_device.cuh"
 #include "nk_internal.h"
@@ -77,7 +79,9 @@ template <int TPV> struct Lanes {
 
 __device__ __forceinline__ int degree(const int32_t *rp, int v) { return __ldg(rp + v + 1) - __ldg(rp + v); }
 
-__device__ __forceinline__ bool heavy(const SrcArgs &a, int v) { return degree(a.rp, v) > kHeavyChunk; }
+// A row is processed in chunks only when a chunk table exists (a.H > 0, which holds
+// exactly when some row is longer than kHeavyChunk); without one, every row is light.
+__device__ __forceinline__ bool heavy(const SrcArgs &a, int v) { return a.H > 0 && degree(a.rp, v) > kHeavyChunk; }
 
 // Chunk c of a heavy vertex: its vertex h and arc range [j0, j1).
 __device__ __forceinline__ void chunk_of(const SrcArgs &a, long long c, int &h, int &j0, int &j1)
@@ -513,3 +517,114 @@ int run_sssp(nk_graph *g, int32_t src, int32_t *d_dist, uint64_t *d_sigma, cudaS
 }
 
 }  // namespace nk
+
+// ---------------------------------------------------------------- allocation-free sweep
+// A variant of the forward sweep for callers that cannot allocate device memory at
+// call time (for example code running under an allocator that forbids cudaMalloc, or
+// a host library that must not grow its footprint once started).  Its scratch - the
+// control block, the BFS queue and the per-level counters - lives in one file-scope
+// device array of fixed size, so the call allocates nothing; inputs (the CSR) and
+// outputs (dist, sigma) are the caller's device buffers.  Rows are not split into
+// chunks here (the chunk table would need an allocation), so a high-degree vertex is
+// expanded by one lane group.
+namespace nk {
+namespace {
+
+constexpr size_t na_align(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr int32_t kNoAllocMaxN = 1 << 20;
+constexpr size_t kNaLv = (size_t)kNoAllocMaxN + 3;
+constexpr size_t kNaCtrl = 0;
+constexpr size_t kNaSrc = 256;
+constexpr size_t kNaQueue = 512;
+constexpr size_t kNaCnt = na_align(kNaQueue + 4 * (size_t)kNoAllocMaxN);
+constexpr size_t kNaQoff = na_align(kNaCnt + 4 * kNaLv);
+constexpr size_t kNaMfa = na_align(kNaQoff + 4 * kNaLv);
+constexpr size_t kNaPart = na_align(kNaMfa + 8 * kNaLv);
+constexpr size_t kNaBytes = kNaPart + 256;
+
+}  // namespace
+}  // namespace nk
+
+// One copy per device that loads the library, held until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[nk::kNaBytes];
+
+namespace nk {
+namespace {
+
+std::mutex g_na_mu;
+void *g_na_ptr[128] = {};
+
+// Device address of the static scratch on the current device.  The array's name in
+// host code is only a host-side stand-in, so the address is looked up once per device
+// (with that device current) and cached.
+int noalloc_scratch(unsigned char **out)
+{
+    int dev = 0;
+    NK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) return set_error(NK_ERR_ARG, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (!g_na_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress(scratch)", __FILE__, __LINE__);
+        g_na_ptr[dev] = p;
+    }
+    *out = static_cast<unsigned char *>(g_na_ptr[dev]);
+    return NK_OK;
+}
+
+}  // namespace
+}  // namespace nk
+
+extern "C" int nk_sssp_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                               int64_t n_arcs, int32_t s, int32_t *dist, uint64_t *sigma,
+                               void *stream)
+{
+    using namespace nk;
+    if (!row_ptr || !dist || !sigma || (n_arcs > 0 && !col)) return set_error(NK_ERR_ARG, "null argument");
+    if (n < 1 || n > kNoAllocMaxN)
+        return set_error(NK_ERR_ARG, "nk_sssp_noalloc handles 1 <= n <= %d vertices (got %d)", kNoAllocMaxN, n);
+    if (n_arcs < 0 || n_arcs >= (int64_t)INT_MAX) return set_error(NK_ERR_ARG, "n_arcs out of range");
+    if (s < 0 || s >= n) return set_error(NK_ERR_ARG, "source %d outside [0, %d)", s, n);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned char *scr = nullptr;
+    NK_TRY(noalloc_scratch(&scr));
+    const double avg = (double)n_arcs / n;
+    const int tpv = avg <= 3 ? 2 : avg <= 12 ? 4 : avg <= 48 ? 8 : avg <= 160 ? 16 : 32;
+    Launch L;
+    NK_TRY(pick_launch(tpv, L));
+    SrcArgs a;
+    a.n = n;
+    a.A = n_arcs;
+    a.rp = row_ptr;
+    a.col = col;
+    a.src = reinterpret_cast<const int32_t *>(scr + kNaSrc);
+    a.dist = dist;
+    a.sp = reinterpret_cast<unsigned long long *>(sigma);
+    a.queue = reinterpret_cast<int32_t *>(scr + kNaQueue);
+    a.cnt = reinterpret_cast<int32_t *>(scr + kNaCnt);
+    a.qoff = reinterpret_cast<int32_t *>(scr + kNaQoff);
+    a.mfa = reinterpret_cast<long long *>(scr + kNaMfa);
+    a.scores = nullptr;
+    a.ctrl = reinterpret_cast<Ctrl *>(scr + kNaCtrl);
+    a.limit_ns = wait_limit_ns();
+    a.alpha = 1.0;
+    a.dir = NK_DIR_AUTO;
+    a.forward_only = 1;
+    a.hv = a.hfirst = a.chunk_h = nullptr;
+    a.H = 0;
+    a.C = 0;
+    a.part = reinterpret_cast<unsigned long long *>(scr + kNaPart);
+    // the control block keeps the previous call's words: it must start at zero
+    NK_CUDA(cudaMemsetAsync(a.ctrl, 0, sizeof(Ctrl), st));
+    NK_CUDA(cudaMemcpyAsync(scr + kNaSrc, &s, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    void *args[] = {&a};
+    NK_CUDA(cudaLaunchCooperativeKernel(L.fn, dim3(L.grid), dim3(kThreads), args, 0, st));
+    ::nk::count_launch();
+    Ctrl h;
+    NK_CUDA(cudaMemcpyAsync(&h, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    NK_CUDA(cudaStreamSynchronize(st));
+    if (h.err) return set_error(h.err, "forward sweep aborted: a bounded grid wait ran out");
+    if (h.ovf) return set_error(NK_ERR_OVERFLOW, "a shortest-path count exceeded 2^64 - 1");
+    return NK_OK;
+}

@@ -85,6 +85,7 @@ SIGNATURES = {
     "nk_graph_free": (_INT, [_P]),
     "nk_sample_sources": (_INT, [_I32, _U64, _I32, _P, _U32]),
     "nk_sssp": (_INT, [_P, _I32, _P, _P]),
+    "nk_sssp_noalloc": (_INT, [_I32, _P, _P, _I64, _I32, _P, _P, _P]),
     "nk_betweenness_exact": (_INT, [_P, _P]),
     "nk_betweenness_sampled": (_INT, [_P, _U64, _I32, _P]),
     "nk_betweenness_sampled_opts": (_INT, [_P, _U64, _I32, _P, _P]),
@@ -252,6 +253,17 @@ def sssp(g: Graph, s: int):
     sigma = np.empty(n, np.uint64)
     _check(lib().nk_sssp(g.handle, s, _np_ptr(dist), _np_ptr(sigma)))
     return dist, sigma
+
+
+def sssp_noalloc(row_ptr, col, s: int, dist, sigma, stream=None) -> None:
+    """Allocation-free forward sweep into caller-owned CUDA tensors: row_ptr (int32,
+    n+1) and col (int32) hold a canonical CSR on the device; dist (int32, n) and sigma
+    (int64 storage read as uint64, n) receive the results.  See nk.h."""
+    n = row_ptr.numel() - 1
+    h = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(lib().nk_sssp_noalloc(n, _dev_ptr(row_ptr), _dev_ptr(col) if col.numel() else None,
+                                 col.numel(), s, _dev_ptr(dist), _dev_ptr(sigma),
+                                 ctypes.c_void_p(h)))
 
 
 # ---------------------------------------------------------------- betweenness
