@@ -9,7 +9,8 @@
 //               level, kept for the backward sweep)
 //   vis[v][q]   union of F_0..F_d
 //   sp[v][b]    sigma_b(v) (uint64) during the forward sweep; replaced by
-//               psi_b(v) = (1 + delta_b(v)) / sigma_b(v) (double) in the backward sweep
+//               psi_b(v) = (1 + delta_b(v)) / sigma_b(v) in the backward sweep (a
+//               double-single pair of floats, see nk_device.cuh)
 //   queue       vertices of the levels found top-down (levels found bottom-up are
 //               iterated by scanning F_d)
 // Forward level d, either
@@ -34,6 +35,8 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "nk_device.cuh"
@@ -48,6 +51,7 @@ constexpr int kThreads = 256;
 constexpr int kErrDepth = 100;  // internal status: BFS deeper than the level slabs
 constexpr int kStartLevels = 48; // level slabs of a first attempt
 constexpr unsigned FULL = 0xffffffffu;
+constexpr int kTraceCap = 1024;
 constexpr int kChunk = kHeavyChunk;  // arcs per work item; longer rows are split
 
 struct BArgs {
@@ -79,6 +83,7 @@ struct BArgs {
     const int32_t *chunk_h;      // [C] heavy index of each chunk
     int32_t H, C;
     unsigned long long *part;    // [C][B] per-chunk partial sums (uint64 or double)
+    unsigned long long *trace;   // [kTraceCap][2] (code, globaltimer) after each barrier, or null
 };
 
 template <int W> struct Bits {
@@ -135,13 +140,13 @@ template <int W> __device__ __forceinline__ bool has_slot(const Bits<W> &b, int 
 
 // For the warp's vertex with adjacency [beg, end): per source slot, the sum of sp over
 // the neighbours c whose Fsel[c] & tgt holds that source bit; uint64 sums (sigma, with
-// carry detection) or double sums (psi).  Lanes over neighbours find the relevant
+// carry detection) or double-single sums (psi).  Lanes over neighbours find the relevant
 // ones; then lanes over source bits read the contiguous sp rows, two neighbours per
 // round so that their loads are in flight together.
 template <int W, bool PSI>
 __device__ __forceinline__ void gather(const BArgs &a, int beg, int end,
                                        const unsigned long long *Fsel, const Bits<W> &tgt,
-                                       unsigned long long (&acc)[2 * W], double (&facc)[2 * W],
+                                       unsigned long long (&acc)[2 * W], dev::ff (&facc)[2 * W],
                                        bool &ovf)
 {
     constexpr int B = 64 * W;
@@ -183,8 +188,8 @@ __device__ __forceinline__ void gather(const BArgs &a, int beg, int end,
 #pragma unroll
             for (int k = 0; k < 2 * W; ++k) {
                 if constexpr (PSI) {
-                    facc[k] += __longlong_as_double((long long)x0[k]);
-                    facc[k] += __longlong_as_double((long long)x1[k]);
+                    facc[k] = dev::ff_add(facc[k], dev::ff_unpack(x0[k]));
+                    facc[k] = dev::ff_add(facc[k], dev::ff_unpack(x1[k]));
                 } else {
                     const unsigned long long y = acc[k] + x0[k];
                     const unsigned long long z = y + x1[k];
@@ -270,6 +275,19 @@ __device__ __forceinline__ void for_level(const BArgs &a, int qo, int nq,
     }
 }
 
+// Phase trace (diagnostics): CTA 0 records (code, %globaltimer) after a grid barrier.
+// code = level * 16 + phase.
+enum { PH_INIT = 1, PH_BU_A, PH_BU_B, PH_TD_A, PH_TD_B, PH_TD_C, PH_BK_A, PH_BK_B };
+
+__device__ __forceinline__ void trace_mark(const BArgs &a, int &ti, int level, int phase)
+{
+    if (a.trace && blockIdx.x == 0 && threadIdx.x == 0 && ti < kTraceCap) {
+        a.trace[2 * ti] = (unsigned long long)(level * 16 + phase);
+        a.trace[2 * ti + 1] = dev::globaltimer();
+        ++ti;
+    }
+}
+
 // Work on the chunks of heavy vertices: fn(c, h, j0, j1) per chunk, with the whole warp.
 template <class Fn> __device__ __forceinline__ void for_chunks(const BArgs &a, Fn fn)
 {
@@ -320,6 +338,8 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
         act.w[q] = left >= 64 ? ~0ull : (left <= 0 ? 0ull : ((1ull << left) - 1));
     }
     bool ovf = false;
+    int ti = 0;
+    trace_mark(a, ti, 0, 0);
     auto flush_counts = [&](int lvl) {
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -344,6 +364,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
         a.dmu[tid] = 0;
     }
     if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+    trace_mark(a, ti, 0, PH_INIT);
     if (tid < a.nsrc) {
         const int s = __ldg(a.src + tid);
         const unsigned long long bit = 1ull << (tid & 63);
@@ -403,7 +424,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
                     const Bits<W> vold = shfl_bits<W>(vv, t);
                     const Bits<W> u = andnot<W>(act, vold);
                     unsigned long long acc[2 * W];
-                    double facc[2 * W];
+                    dev::ff facc[2 * W];
 #pragma unroll
                     for (int k = 0; k < 2 * W; ++k) acc[k] = 0;
                     gather<W, false>(a, __ldg(a.rp + w), __ldg(a.rp + w + 1), Fd, u, acc, facc, ovf);
@@ -415,13 +436,14 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
                 const Bits<W> u = andnot<W>(act, load_bits<W>(a.vis + (size_t)h * W));
                 if (!any_bits<W>(u)) return;
                 unsigned long long acc[2 * W];
-                double facc[2 * W];
+                dev::ff facc[2 * W];
 #pragma unroll
                 for (int k = 0; k < 2 * W; ++k) acc[k] = 0;
                 gather<W, false>(a, j0, j1, Fd, u, acc, facc, ovf);
                 store_part<W>(a, c, acc);
             });
             if (a.H > 0 && !dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+            trace_mark(a, ti, d, PH_BU_A);
             // ---- bottom-up (b): heavy vertices sum their chunks in chunk order
             for_heavy(a, [&](int i, int h, int c0, int c1) {
                 const Bits<W> vold = load_bits<W>(a.vis + (size_t)h * W);
@@ -444,6 +466,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
             flush_counts(d + 1);
             if (tid == 0) a.qoff[d + 1] = -1;
             if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+            trace_mark(a, ti, d, PH_BU_B);
         } else {
             // ---- top-down (a): push the frontier's bits, queue each new vertex once;
             //      heavy frontier vertices push chunk by chunk
@@ -473,6 +496,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
                 if (any_bits<W>(load_bits<W>(Fd + (size_t)h * W))) push(h, j0, j1);
             });
             if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+            trace_mark(a, ti, d, PH_TD_A);
             // ---- top-down (b): every new vertex pulls sigma for its new bits
             nq1 = __ldcg(a.qcnt + d + 1);
             queued = qtail + nq1 <= a.qcap;
@@ -481,7 +505,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
                 const Bits<W> t = load_bits<W>(Fn + (size_t)w * W);
                 const Bits<W> vold = load_bits<W>(a.vis + (size_t)w * W);
                 unsigned long long acc[2 * W];
-                double facc[2 * W];
+                dev::ff facc[2 * W];
 #pragma unroll
                 for (int k = 0; k < 2 * W; ++k) acc[k] = 0;
                 gather<W, false>(a, __ldg(a.rp + w), __ldg(a.rp + w + 1), Fd, t, acc, facc, ovf);
@@ -491,13 +515,14 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
                 const Bits<W> t = load_bits<W>(Fn + (size_t)h * W);
                 if (!any_bits<W>(t)) return;
                 unsigned long long acc[2 * W];
-                double facc[2 * W];
+                dev::ff facc[2 * W];
 #pragma unroll
                 for (int k = 0; k < 2 * W; ++k) acc[k] = 0;
                 gather<W, false>(a, j0, j1, Fd, t, acc, facc, ovf);
                 store_part<W>(a, c, acc);
             });
             if (a.H > 0 && !dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+            trace_mark(a, ti, d, PH_TD_B);
             // ---- top-down (c): heavy new vertices sum their chunks in chunk order
             for_heavy(a, [&](int i, int h, int c0, int c1) {
                 const Bits<W> t = load_bits<W>(Fn + (size_t)h * W);
@@ -520,6 +545,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
             flush_counts(d + 1);
             if (tid == 0) a.qoff[d + 1] = queued ? (int)qtail : -1;
             if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+            trace_mark(a, ti, d, PH_TD_C);
         }
         const int c = __ldcg(a.vcnt + d + 1);
         if (use_bu) {
@@ -556,28 +582,31 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
         const int ql = __ldcg(a.qoff + l);
         const int nl = ql >= 0 ? __ldcg(a.qcnt + l) : 0;
         // delta/psi/score of vertex v from its successor sums facc (whole warp)
-        auto finish = [&](int v, const Bits<W> &mv, const double (&facc)[2 * W]) {
-            double part = 0.0;
+        // psi_v = 1/sigma_v + acc and delta_v = sigma_v * acc (Brandes' recurrence with
+        // sigma_v factored out), in double-single; the vertex's delta summed over its
+        // source slots goes to the FP64 score once per vertex and level
+        auto finish = [&](int v, const Bits<W> &mv, const dev::ff (&facc)[2 * W]) {
+            dev::ff part = dev::ff_zero();
             unsigned long long *row = a.sp + (size_t)v * B + lane;
 #pragma unroll
             for (int k = 0; k < 2 * W; ++k) {
                 if (has_slot<W>(mv, k, lane)) {
-                    const double sv = __ull2double_rn(__ldcg(row + 32 * k));
-                    const double delta = __dmul_rn(sv, facc[k]);
-                    row[32 * k] = (unsigned long long)__double_as_longlong(__ddiv_rn(__dadd_rn(1.0, delta), sv));
-                    part += delta;
+                    const dev::ff sv = dev::ff_from_u64(__ldcg(row + 32 * k));
+                    const dev::ff delta = dev::ff_mul(sv, facc[k]);
+                    row[32 * k] = dev::ff_pack(dev::ff_add(dev::ff_rcp(sv), facc[k]));
+                    part = dev::ff_add(part, delta);
                 }
             }
-            part = dev::group_sum<32>(part);
-            if (lane == 0 && part != 0.0) a.scores[v] += part;
+            part = dev::group_sum_ff<32>(part);
+            if (lane == 0 && part.hi != 0.0f) a.scores[v] += dev::ff_to_double(part);
         };
         for_level<W>(a, ql, nl, Fl, [&](int v) {
             if (heavy(a, v)) return;
             const Bits<W> mv = load_bits<W>(Fl + (size_t)v * W);
             unsigned long long acc[2 * W];
-            double facc[2 * W];
+            dev::ff facc[2 * W];
 #pragma unroll
-            for (int k = 0; k < 2 * W; ++k) facc[k] = 0.0;
+            for (int k = 0; k < 2 * W; ++k) facc[k] = dev::ff_zero();
             bool dummy = false;
             gather<W, true>(a, __ldg(a.rp + v), __ldg(a.rp + v + 1), Fs, mv, acc, facc, dummy);
             finish(v, mv, facc);
@@ -586,30 +615,32 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
             const Bits<W> mv = load_bits<W>(Fl + (size_t)h * W);
             if (!any_bits<W>(mv)) return;
             unsigned long long acc[2 * W];
-            double facc[2 * W];
+            dev::ff facc[2 * W];
 #pragma unroll
-            for (int k = 0; k < 2 * W; ++k) facc[k] = 0.0;
+            for (int k = 0; k < 2 * W; ++k) facc[k] = dev::ff_zero();
             bool dummy = false;
             gather<W, true>(a, j0, j1, Fs, mv, acc, facc, dummy);
 #pragma unroll
-            for (int k = 0; k < 2 * W; ++k) acc[k] = (unsigned long long)__double_as_longlong(facc[k]);
+            for (int k = 0; k < 2 * W; ++k) acc[k] = dev::ff_pack(facc[k]);
             store_part<W>(a, c, acc);
         });
         if (a.H > 0 && !dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+        trace_mark(a, ti, l, PH_BK_A);
         for_heavy(a, [&](int i, int h, int c0, int c1) {
             const Bits<W> mv = load_bits<W>(Fl + (size_t)h * W);
             if (!any_bits<W>(mv)) return;
-            double facc[2 * W];
+            dev::ff facc[2 * W];
 #pragma unroll
-            for (int k = 0; k < 2 * W; ++k) facc[k] = 0.0;
+            for (int k = 0; k < 2 * W; ++k) facc[k] = dev::ff_zero();
             for (int c = c0; c < c1; ++c) {
                 const unsigned long long *row = a.part + (size_t)c * B + lane;
 #pragma unroll
-                for (int k = 0; k < 2 * W; ++k) facc[k] += __longlong_as_double((long long)__ldcg(row + 32 * k));
+                for (int k = 0; k < 2 * W; ++k) facc[k] = dev::ff_add(facc[k], dev::ff_unpack(__ldcg(row + 32 * k)));
             }
             finish(h, mv, facc);
         });
         if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+        trace_mark(a, ti, l, PH_BK_B);
     }
 }
 
@@ -705,6 +736,12 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
     std::vector<int> todo(nb);
     for (int bi = 0; bi < nb; ++bi) todo[bi] = bi;
     double alpha_used = cfg.alpha > 0 ? cfg.alpha : 1.0;
+    static const bool trace_on = std::getenv("NK_TRACE") != nullptr;
+    Tmp trace_buf;
+    if (trace_on) {
+        NK_TRY(trace_buf.alloc(sizeof(unsigned long long) * 2 * kTraceCap, s));
+        NK_CUDA(cudaMemsetAsync(trace_buf.p, 0, sizeof(unsigned long long) * 2 * kTraceCap, s));
+    }
     for (int lcap = lstart;;) {
         const Layout L = layout(g, B, lcap);
         NK_TRY(ws[WS_BATCH].ensure(L.total));
@@ -735,6 +772,7 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
         a.H = g->heavy_H;
         a.C = g->heavy_C;
         a.part = reinterpret_cast<unsigned long long *>(base + L.off_part);
+        a.trace = nullptr;
         a.limit_ns = cfg.limit_ns ? cfg.limit_ns : wait_limit_ns();
         a.alpha = alpha_used;
         a.dir = cfg.direction;
@@ -749,6 +787,7 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
             a.src = d_src + (size_t)bi * B;
             a.nsrc = std::min(B, k - bi * B);
             a.ctrl = ctrls + bi;
+            a.trace = (trace_on && bi == todo.front()) ? trace_buf.as<unsigned long long>() : nullptr;
             void *args[] = {&a};
             NK_CUDA(cudaLaunchCooperativeKernel((const void *)k_batch<W>, dim3(grid), dim3(kThreads), args, 0, s));
             ::nk::count_launch();
@@ -776,6 +815,15 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
         }
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
+        if (trace_on) {
+            static const char *names[] = {"start", "init", "bu-pull", "bu-hubs", "td-push", "td-pull", "td-hubs", "back", "back-hubs"};
+            std::vector<unsigned long long> t(2 * kTraceCap);
+            NK_CUDA(cudaMemcpyAsync(t.data(), trace_buf.p, sizeof(unsigned long long) * t.size(), cudaMemcpyDeviceToHost, s));
+            NK_CUDA(cudaStreamSynchronize(s));
+            for (int i = 1; i < kTraceCap && t[2 * i + 1]; ++i)
+                fprintf(stderr, "nk-trace B=%d level=%llu phase=%s us=%.1f\n", B, t[2 * i] / 16,
+                        names[std::min<unsigned long long>(t[2 * i] % 16, 8)], (t[2 * i + 1] - t[2 * i - 1]) * 1e-3);
+        }
         bool ovf = false;
         std::vector<int> deep;
         for (int bi : todo) {

@@ -117,6 +117,87 @@ template <int W> __device__ __forceinline__ uint64_t group_sum_u64(uint64_t x, b
     return x;
 }
 
+// ---------------------------------------------------------------- double-single numbers
+// A value held as the unevaluated sum hi + lo of two floats (about 48 significant bits),
+// after Dekker ("A floating-point technique for extending the available precision",
+// 1971) and Knuth's TwoSum (TAOCP vol. 2, 4.2.2).  The backward sweep accumulates its
+// dependency sums in this form on the FP32 pipe: on this GPU the FP64 pipe issues about
+// two lanes per clock per SM, so one warp-wide FP64 add costs ~16 SM clocks, while the
+// ~11 FP32 operations of a double-single add cost ~3.  Every operation is explicitly
+// rounded so that the compiler cannot contract or reorder it.  All operands on the
+// betweenness path are non-negative, where these forms are accurate to ~2^-44 relative.
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_zero() { return {0.0f, 0.0f}; }
+
+// s + t with |s| >= |t| (FastTwoSum): renormalised pair
+__device__ __forceinline__ ff ff_fast2sum(float s, float t)
+{
+    const float hi = __fadd_rn(s, t);
+    return {hi, __fsub_rn(t, __fsub_rn(hi, s))};
+}
+
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float v = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v));  // TwoSum error
+    return ff_fast2sum(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ ff ff_mul(ff a, ff b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    const float e = __fmaf_rn(a.hi, b.hi, -p);  // exact error of the leading product
+    return ff_fast2sum(p, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e)));
+}
+
+// 1/x: the float reciprocal of x.hi refined by one Newton step r + r(1 - x r) carried
+// out in double-single (1 - x.hi r is exact by Sterbenz, its FMA error term is exact).
+__device__ __forceinline__ ff ff_rcp(ff x)
+{
+    const float r0 = __frcp_rn(x.hi);
+    const float p = __fmul_rn(x.hi, r0);
+    const float pe = __fmaf_rn(x.hi, r0, -p);
+    const float e = __fsub_rn(__fsub_rn(__fsub_rn(1.0f, p), pe), __fmul_rn(x.lo, r0));
+    return ff_fast2sum(r0, __fmul_rn(r0, e));
+}
+
+// exact-to-~2^-47 conversion of a path count: truncated leading float plus the rounded
+// integer remainder
+__device__ __forceinline__ ff ff_from_u64(unsigned long long x)
+{
+    const float hi = __ull2float_rz(x);
+    const float lo = __ull2float_rn(x - __float2ull_rz(hi));
+    return ff_fast2sum(hi, lo);
+}
+
+__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
+
+// 8-byte storage: hi in the low word, lo in the high word
+__device__ __forceinline__ unsigned long long ff_pack(ff a)
+{
+    return ((unsigned long long)__float_as_uint(a.lo) << 32) | __float_as_uint(a.hi);
+}
+__device__ __forceinline__ ff ff_unpack(unsigned long long u)
+{
+    return {__uint_as_float((unsigned)(u & 0xffffffffu)), __uint_as_float((unsigned)(u >> 32))};
+}
+
+template <int W> __device__ __forceinline__ ff group_sum_ff(ff x)
+{
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) {
+        ff y;
+        y.hi = __shfl_xor_sync(0xffffffffu, x.hi, o, W);
+        y.lo = __shfl_xor_sync(0xffffffffu, x.lo, o, W);
+        x = ff_add(x, y);
+    }
+    return x;
+}
+
 __device__ __forceinline__ unsigned lanemask_lt()
 {
     unsigned m;

@@ -20,7 +20,8 @@
 //               acc = sum_{w in N(v), dist w = d+1} psi[w],  psi = (1 + delta) / sigma,
 //               delta_s(v) = sigma[v] * acc,  scores[v] += delta_s(v),
 //             which is Brandes' recurrence delta(v) = sum sigma_v/sigma_w (1 + delta_w)
-//             with the common factor sigma_v taken out.  psi overwrites sigma in place
+//             with the common factor sigma_v taken out; psi_v = 1/sigma_v + acc.  The
+//             sums run in double-single arithmetic (FP32 pipe), scores in FP64.  psi overwrites sigma in place
 //             once a vertex's level is done (sigma of level d is still intact while
 //             level d reads psi of level d+1).
 // The levels are separated by a bounded grid barrier; per-level counters live in
@@ -221,6 +222,17 @@ __device__ void bu_heavy_finish(const SrcArgs &a, int d, int *s_cnt, unsigned lo
     }
 }
 
+// psi_v = 1/sigma_v + acc and delta_v = sigma_v * acc (Brandes' recurrence with sigma_v
+// factored out), in double-single arithmetic; psi overwrites sigma, delta goes to the
+// FP64 score.
+__device__ __forceinline__ void finish_vertex(const SrcArgs &a, int v, dev::ff acc)
+{
+    const dev::ff sv = dev::ff_from_u64(dev::ldcg(a.sp + v));
+    const dev::ff delta = dev::ff_mul(sv, acc);
+    a.sp[v] = dev::ff_pack(dev::ff_add(dev::ff_rcp(sv), acc));
+    if (delta.hi != 0.0f) a.scores[v] += dev::ff_to_double(delta);
+}
+
 // ------------------------------------------------------------------ backward level d
 template <int TPV>
 __device__ void back_level(const SrcArgs &a, int d, int qo, int nd)
@@ -236,34 +248,29 @@ __device__ void back_level(const SrcArgs &a, int d, int qo, int nd)
             else if (dev::ldcg(a.dist + item) == d) v = (int)item;
             if (v >= 0 && heavy(a, v)) v = -1;
         }
-        double acc = 0.0;
+        dev::ff acc = dev::ff_zero();
         if (v >= 0) {
             const int beg = __ldg(a.rp + v), end = __ldg(a.rp + v + 1);
             for (int j = beg + L.lg; j < end; j += TPV) {
                 const int w = __ldg(a.col + j);
-                if (dev::ldcg(a.dist + w) == d + 1) acc += __longlong_as_double((long long)dev::ldcg(a.sp + w));
+                if (dev::ldcg(a.dist + w) == d + 1) acc = dev::ff_add(acc, dev::ff_unpack(dev::ldcg(a.sp + w)));
             }
         }
-        acc = dev::group_sum<TPV>(acc);
-        if (v >= 0 && L.lg == 0) {
-            const double sv = __ull2double_rn(dev::ldcg(a.sp + v));
-            const double delta = __dmul_rn(sv, acc);
-            a.sp[v] = (unsigned long long)__double_as_longlong(__ddiv_rn(__dadd_rn(1.0, delta), sv));
-            if (delta != 0.0) a.scores[v] += delta;
-        }
+        acc = dev::group_sum_ff<TPV>(acc);
+        if (v >= 0 && L.lg == 0) finish_vertex(a, v, acc);
     }
     // heavy vertices of level d: per-chunk partial sums of psi
     for (long long c = L.wid; c < a.C; c += L.nw) {
         int h, j0, j1;
         chunk_of(a, c, h, j0, j1);
         if (dev::ldcg(a.dist + h) != d) continue;
-        double acc = 0.0;
+        dev::ff acc = dev::ff_zero();
         for (int j = j0 + L.lane; j < j1; j += 32) {
             const int w = __ldg(a.col + j);
-            if (dev::ldcg(a.dist + w) == d + 1) acc += __longlong_as_double((long long)dev::ldcg(a.sp + w));
+            if (dev::ldcg(a.dist + w) == d + 1) acc = dev::ff_add(acc, dev::ff_unpack(dev::ldcg(a.sp + w)));
         }
-        acc = dev::group_sum<32>(acc);
-        if (L.lane == 0) a.part[c] = (unsigned long long)__double_as_longlong(acc);
+        acc = dev::group_sum_ff<32>(acc);
+        if (L.lane == 0) a.part[c] = dev::ff_pack(acc);
     }
 }
 
@@ -274,13 +281,10 @@ __device__ void back_heavy_finish(const SrcArgs &a, int d)
          i += (long long)gridDim.x * blockDim.x) {
         const int h = __ldg(a.hv + i);
         if (dev::ldcg(a.dist + h) != d) continue;
-        double acc = 0.0;
+        dev::ff acc = dev::ff_zero();
         for (int c = __ldg(a.hfirst + i); c < __ldg(a.hfirst + i + 1); ++c)
-            acc += __longlong_as_double((long long)dev::ldcg(a.part + c));
-        const double sv = __ull2double_rn(dev::ldcg(a.sp + h));
-        const double delta = __dmul_rn(sv, acc);
-        a.sp[h] = (unsigned long long)__double_as_longlong(__ddiv_rn(__dadd_rn(1.0, delta), sv));
-        if (delta != 0.0) a.scores[h] += delta;
+            acc = dev::ff_add(acc, dev::ff_unpack(dev::ldcg(a.part + c)));
+        finish_vertex(a, h, acc);
     }
 }
 
