@@ -138,6 +138,19 @@ template <int W> __device__ __forceinline__ bool has_slot(const Bits<W> &b, int 
     return (b.w[k >> 1] >> (((k & 1) << 5) + lane)) & 1ull;
 }
 
+// The same test on the 32-bit half-word that holds slot k, with lanebit = 1 << lane.
+template <int W> __device__ __forceinline__ bool slot_bit(const Bits<W> &b, int k, unsigned lanebit)
+{
+    const unsigned half = (k & 1) ? (unsigned)(b.w[k >> 1] >> 32) : (unsigned)b.w[k >> 1];
+    return (half & lanebit) != 0;
+}
+
+// acc += x with the carry out of bit 63 counted in carry (a path-count overflow).
+__device__ __forceinline__ void add_carry(unsigned long long &acc, unsigned &carry, unsigned long long x)
+{
+    asm("add.cc.u64 %0, %0, %2;\n\taddc.u32 %1, %1, 0;" : "+l"(acc), "+r"(carry) : "l"(x));
+}
+
 // For the warp's vertex with adjacency [beg, end): per source slot, the sum of sp over
 // the neighbours c whose Fsel[c] & tgt holds that source bit; uint64 sums (sigma, with
 // carry detection) or double-single sums (psi).  Lanes over neighbours find the relevant
@@ -151,6 +164,8 @@ __device__ __forceinline__ void gather(const BArgs &a, int beg, int end,
 {
     constexpr int B = 64 * W;
     const int lane = threadIdx.x & 31;
+    const unsigned lanebit = 1u << lane;
+    unsigned carry = 0;
     for (int base = beg; base < end; base += 32) {
         const int j = base + lane;
         int c = 0;
@@ -182,8 +197,8 @@ __device__ __forceinline__ void gather(const BArgs &a, int beg, int end,
             unsigned long long x0[2 * W], x1[2 * W];
 #pragma unroll
             for (int k = 0; k < 2 * W; ++k) {
-                x0[k] = has_slot<W>(f0, k, lane) ? __ldcg(r0 + 32 * k) : 0ull;
-                x1[k] = (two && has_slot<W>(f1, k, lane)) ? __ldcg(r1 + 32 * k) : 0ull;
+                x0[k] = slot_bit<W>(f0, k, lanebit) ? __ldcg(r0 + 32 * k) : 0ull;
+                x1[k] = (two && slot_bit<W>(f1, k, lanebit)) ? __ldcg(r1 + 32 * k) : 0ull;
             }
 #pragma unroll
             for (int k = 0; k < 2 * W; ++k) {
@@ -191,14 +206,13 @@ __device__ __forceinline__ void gather(const BArgs &a, int beg, int end,
                     facc[k] = dev::ff_add(facc[k], dev::ff_unpack(x0[k]));
                     facc[k] = dev::ff_add(facc[k], dev::ff_unpack(x1[k]));
                 } else {
-                    const unsigned long long y = acc[k] + x0[k];
-                    const unsigned long long z = y + x1[k];
-                    ovf |= (y < acc[k]) | (z < y);
-                    acc[k] = z;
+                    add_carry(acc[k], carry, x0[k]);
+                    add_carry(acc[k], carry, x1[k]);
                 }
             }
         }
     }
+    if (!PSI) ovf |= carry != 0;
 }
 
 template <int W> __device__ __forceinline__ Bits<W> nonzero_bits(const unsigned long long (&acc)[2 * W])
