@@ -160,6 +160,32 @@ def per_source_bytes(n, A):
     return 8.0 * A + 64.0 * n
 
 
+def kernel_source_hash(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def committed_traffic(config, batch):
+    """DRAM bytes per launch of the batched kernel from the committed ncu summary, or
+    None when there is none for this workload and batch size or the kernel's source has
+    changed since the counters were taken."""
+    prof = os.path.join(ROOT, "profiles", f"k_batch_{config}_traffic.json")
+    try:
+        with open(prof) as f:
+            pj = json.load(f)
+        if pj.get("batch") != batch:
+            return None
+        if pj.get("kernel_source_sha256") != kernel_source_hash(pj["kernel_sources"]):
+            return None
+        return pj.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -361,16 +387,7 @@ def run_ours(args, world, rank, local):
     per_launch_ms = kern_ms / max(launches, 1)
     alg = algorithmic_bytes_per_launch(n, A, B)
     achieved = alg / (per_launch_ms / 1e3) / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", f"k_batch_{args.config}_traffic.json")
-    if os.path.exists(prof):
-        try:
-            with open(prof) as f:
-                pj = json.load(f)
-            if pj.get("batch") == B:
-                traffic = pj.get("dram_bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = committed_traffic(args.config, B)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": f"k_batch<W={B // 64}>", "peak_kind": peak_kind,

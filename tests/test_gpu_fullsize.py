@@ -1,0 +1,103 @@
+"""Parity at the benchmark workloads' full sizes, in the launch configuration bench.py
+times (batched form, autotuned batch and switch threshold).
+
+Where the oracle can compute outputs one by one (a source subset of the same sampled
+set, on the oracle's own copy of the graph), they are compared element by element;
+otherwise properties that hold at any size are checked on the GPU outputs.  The oracle
+never receives a GPU output.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+RTOL, ATOL = 1e-9, 1e-12
+
+
+@pytest.fixture(scope="module")
+def nk():
+    import torch
+    assert torch.cuda.is_available()
+    torch.cuda.set_device(0)
+    from paper_1403_3005_gb300 import nk as _nk
+    _nk.lib()
+    return _nk
+
+
+def close(a, b):
+    return np.allclose(a, b, rtol=RTOL, atol=ATOL)
+
+
+def test_rmat18_sampled_k1024_full_vector(nk):
+    # the default bench workload: every score of the k = 1024 sampled estimate
+    g = nk.graph_generate("rmat", 18, 1)
+    n, rp, col = oracle.generate("rmat", 18, 1)
+    opts = nk.autotune(g, 2, 1024)
+    got = nk.betweenness_sampled(g, 2, 1024, opts)
+    src = oracle.sample_sources(n, 2, 1024)
+    # the oracle on 4 slices of the source set, summed (sources are independent)
+    import concurrent.futures as cf
+    parts = np.array_split(src, 4)
+    with cf.ThreadPoolExecutor(4) as ex:
+        sums = list(ex.map(lambda p: oracle.betweenness_sources(rp, col, p, 1.0), parts))
+    want = sum(sums) * (n / (2.0 * 1024))
+    assert close(got, want)
+
+
+def test_ba_1m_sources_subset(nk):
+    # BA n = 1e6, m0 = 8: 96 sources of the k = 4096 sample (one full batch + a ragged one)
+    g = nk.graph_generate("ba", 1000000, 1, m0=8)
+    n, rp, col = oracle.generate("ba", 1000000, 1, m0=8)
+    src = oracle.sample_sources(n, 2, 4096)[:96]
+    want = oracle.betweenness_sources(rp, col, src, 1.0)
+    for batch in (64, 128):
+        got = nk.betweenness_sources(g, src, 1.0, nk.run_opts(mode=nk.MODE_BATCHED, batch=batch))
+        assert close(got, want), batch
+    got = nk.betweenness_sources(g, src[:8], 1.0, nk.run_opts(mode=nk.MODE_PER_SOURCE))
+    assert close(got, oracle.betweenness_sources(rp, col, src[:8], 1.0))
+
+
+def test_rmat24_properties(nk):
+    # R-MAT scale 24: the raw edges the oracle computes one by one are in the GPU CSR,
+    # the CSR is canonical, and the batched scores satisfy the pair-distance invariant
+    # of their own sources and vanish on leaves.
+    g = nk.graph_generate("rmat", 24, 1)
+    n, A = g.info()
+    rp, col = g.export_csr()
+    assert rp[0] == 0 and rp[-1] == A and A % 2 == 0
+    deg = np.diff(rp).astype(np.int64)
+    # sample rows: sorted, no duplicates, no self-loop, symmetric
+    rng = np.random.default_rng(0)
+    for v in rng.choice(np.flatnonzero(deg > 0), 2000, replace=False):
+        row = col[rp[v]:rp[v + 1]]
+        assert np.all(np.diff(row) > 0) and not np.any(row == v)
+        for w in row[:4]:
+            r2 = col[rp[w]:rp[w + 1]]
+            assert r2[np.searchsorted(r2, v)] == v
+    # the first 20000 raw edges, computed by the oracle, are present
+    from oracle import _load
+    import ctypes
+    E = 20000
+    u = np.empty(E, np.int32)
+    w = np.empty(E, np.int32)
+    L = _load()
+    L.or_gen_rmat(24, 16, 0.57, 0.19, 0.19, 1, u.ctypes.data_as(ctypes.c_void_p),
+                  w.ctypes.data_as(ctypes.c_void_p), E)
+    for a, b in zip(u.tolist(), w.tolist()):
+        if a != b:
+            r = col[rp[a]:rp[a + 1]]
+            assert r[np.searchsorted(r, b)] == b
+    # scores of 128 sampled sources: sum invariant with the GPU's own distances, leaves 0
+    src = nk.sample_sources(n, 2, 128)
+    sc = nk.betweenness_sources(g, src, 1.0, nk.run_opts(mode=nk.MODE_BATCHED, batch=128))
+    assert np.all(sc >= 0) and np.all(sc[deg == 1] == 0) and np.all(sc[deg == 0] == 0)
+    tot = 0
+    for s in src[:16]:
+        d, _ = nk.sssp(g, int(s))
+        r = d[d > 0].astype(np.int64)
+        tot += int(np.sum(r - 1))
+    part = nk.betweenness_sources(g, src[:16], 1.0, nk.run_opts(mode=nk.MODE_BATCHED, batch=64))
+    assert np.isclose(part.sum(), tot, rtol=1e-9)
