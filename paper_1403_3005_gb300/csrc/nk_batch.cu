@@ -53,6 +53,11 @@ constexpr int kStartLevels = 48; // level slabs of a first attempt
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kTraceCap = 1024;
 constexpr int kChunk = kHeavyChunk;  // arcs per work item; longer rows are split
+constexpr int kGrabQ = 8;            // queue entries a warp takes at a time
+constexpr int kGrabV = 64;           // vertices a warp scans at a time
+constexpr int kGrabC = 2;            // heavy chunks a warp takes at a time
+// work-counter slots of a level
+enum { WQ_BU = 0, WQ_BU_C, WQ_PUSH, WQ_PUSH_C, WQ_PULL, WQ_PULL_C, WQ_BACK, WQ_BACK_C };
 
 struct BArgs {
     int32_t n;
@@ -72,6 +77,7 @@ struct BArgs {
     int32_t *qoff;               // [lcap+3] start of level d in queue, -1 if not queued
     unsigned long long *mfv;     // [lcap+3] sum of degrees of the level-d vertices
     unsigned long long *dmu;     // [lcap+3] degrees of vertices completed at level d
+    int32_t *wq;                 // [lcap+3][8] work counters of the phases of level d
     double *scores;
     Ctrl *ctrl;
     uint64_t limit_ns;
@@ -266,24 +272,40 @@ __device__ __forceinline__ void settle(const BArgs &a, int w, const Bits<W> &vol
 
 // Calls fn(v) with the whole warp for every vertex of a level: the queued entries
 // queue[qo, qo+nq) or, if qo < 0, every v with Fl[v] != 0 (scanned 32 at a time).
+// Calls fn(v) with the whole warp for every vertex of a level: the queued entries
+// queue[qo, qo+nq) or, if qo < 0, every v with Fl[v] != 0 (scanned 32 at a time).  Warps
+// take work dynamically from the zeroed counter *ctr (8 entries or 64 vertices at a
+// time), so that power-law degrees do not leave a few warps finishing long after the
+// rest.
 template <int W, class Fn>
 __device__ __forceinline__ void for_level(const BArgs &a, int qo, int nq,
-                                          const unsigned long long *Fl, Fn fn)
+                                          const unsigned long long *Fl, int32_t *ctr, Fn fn)
 {
     const int lane = threadIdx.x & 31;
-    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     if (qo >= 0) {
-        for (long long i = wid; i < nq; i += nw) fn(__ldcg(a.queue + qo + i));
+        for (;;) {
+            int i0 = 0;
+            if (lane == 0) i0 = atomicAdd(ctr, kGrabQ);
+            i0 = __shfl_sync(FULL, i0, 0);
+            if (i0 >= nq) break;
+            const int i1 = min(i0 + kGrabQ, nq);
+            for (int i = i0; i < i1; ++i) fn(__ldcg(a.queue + qo + i));
+        }
     } else {
-        for (long long base = wid * 32; base < a.n; base += nw * 32) {
-            const long long v = base + lane;
-            const bool nz = v < a.n && any_bits<W>(load_bits<W>(Fl + (size_t)v * W));
-            unsigned m = __ballot_sync(FULL, nz);
-            while (m) {
-                const int t = __ffs(m) - 1;
-                m &= m - 1;
-                fn((int)(base + t));
+        for (;;) {
+            int t0 = 0;
+            if (lane == 0) t0 = atomicAdd(ctr, kGrabV);
+            t0 = __shfl_sync(FULL, t0, 0);
+            if (t0 >= a.n) break;
+            for (int base = t0; base < min(t0 + kGrabV, a.n); base += 32) {
+                const int v = base + lane;
+                const bool nz = v < a.n && any_bits<W>(load_bits<W>(Fl + (size_t)v * W));
+                unsigned m = __ballot_sync(FULL, nz);
+                while (m) {
+                    const int t = __ffs(m) - 1;
+                    m &= m - 1;
+                    fn(base + t);
+                }
             }
         }
     }
@@ -302,17 +324,23 @@ __device__ __forceinline__ void trace_mark(const BArgs &a, int &ti, int level, i
     }
 }
 
-// Work on the chunks of heavy vertices: fn(c, h, j0, j1) per chunk, with the whole warp.
-template <class Fn> __device__ __forceinline__ void for_chunks(const BArgs &a, Fn fn)
+// Work on the chunks of heavy vertices: fn(c, h, j0, j1) per chunk, with the whole warp;
+// chunks are taken dynamically from the zeroed counter *ctr.
+template <class Fn> __device__ __forceinline__ void for_chunks(const BArgs &a, int32_t *ctr, Fn fn)
 {
-    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long c = wid; c < a.C; c += nw) {
-        const int i = __ldg(a.chunk_h + c);
-        const int h = __ldg(a.hv + i);
-        const int j0 = __ldg(a.rp + h) + (int)(c - __ldg(a.hfirst + i)) * kChunk;
-        const int j1 = min(j0 + kChunk, __ldg(a.rp + h + 1));
-        fn((int)c, h, j0, j1);
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int c0 = 0;
+        if (lane == 0) c0 = atomicAdd(ctr, kGrabC);
+        c0 = __shfl_sync(FULL, c0, 0);
+        if (c0 >= a.C) break;
+        for (int c = c0; c < min(c0 + kGrabC, a.C); ++c) {
+            const int i = __ldg(a.chunk_h + c);
+            const int h = __ldg(a.hv + i);
+            const int j0 = __ldg(a.rp + h) + (c - __ldg(a.hfirst + i)) * kChunk;
+            const int j1 = min(j0 + kChunk, __ldg(a.rp + h + 1));
+            fn(c, h, j0, j1);
+        }
     }
 }
 
@@ -370,6 +398,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
         a.F[slab + i] = 0;
     }
     for (long long i = tid; i < a.n; i += nthr) a.qmark[i] = -1;
+    if (tid < 3 * 8) a.wq[tid] = 0;
     if (tid < 3) {
         a.vcnt[tid] = 0;
         a.qcnt[tid] = 0;
@@ -412,6 +441,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
             a.mfv[d + 2] = 0;
             a.dmu[d + 2] = 0;
         }
+        if (tid < 8) a.wq[(size_t)(d + 2) * 8 + tid] = 0;
         {
             unsigned long long *Fz = a.F + (size_t)(d + 2) * slab;
             for (size_t i = tid; i < slab; i += nthr) Fz[i] = 0;
@@ -426,7 +456,11 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
         if (use_bu) {
             // ---- bottom-up (a): light vertices with unvisited sources pull from level d;
             //      chunks of heavy vertices store partial sums
-            for (long long base = wid * 32; base < a.n; base += nw * 32) {
+            for (int t0 = 0;;) {
+                if (lane == 0) t0 = atomicAdd(a.wq + (size_t)d * 8 + WQ_BU, 32);
+                t0 = __shfl_sync(FULL, t0, 0);
+                if (t0 >= a.n) break;
+                const long long base = t0;
                 const long long v = base + lane;
                 Bits<W> vv = act;
                 if (v < a.n && !heavy(a, (int)v)) vv = load_bits<W>(a.vis + (size_t)v * W);
@@ -446,7 +480,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
                     if (any_bits<W>(nb)) settle<W>(a, w, vold, nb, act, acc, Fn, &bc);
                 }
             }
-            for_chunks(a, [&](int c, int h, int j0, int j1) {
+            for_chunks(a, a.wq + (size_t)d * 8 + WQ_BU_C, [&](int c, int h, int j0, int j1) {
                 const Bits<W> u = andnot<W>(act, load_bits<W>(a.vis + (size_t)h * W));
                 if (!any_bits<W>(u)) return;
                 unsigned long long acc[2 * W];
@@ -502,11 +536,11 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
                     }
                 }
             };
-            for_level<W>(a, qo, nq, Fd, [&](int v) {
+            for_level<W>(a, qo, nq, Fd, a.wq + (size_t)d * 8 + WQ_PUSH, [&](int v) {
                 if (heavy(a, v)) return;
                 push(v, __ldg(a.rp + v), __ldg(a.rp + v + 1));
             });
-            for_chunks(a, [&](int c, int h, int j0, int j1) {
+            for_chunks(a, a.wq + (size_t)d * 8 + WQ_PUSH_C, [&](int c, int h, int j0, int j1) {
                 if (any_bits<W>(load_bits<W>(Fd + (size_t)h * W))) push(h, j0, j1);
             });
             if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
@@ -514,7 +548,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
             // ---- top-down (b): every new vertex pulls sigma for its new bits
             nq1 = __ldcg(a.qcnt + d + 1);
             queued = qtail + nq1 <= a.qcap;
-            for_level<W>(a, queued ? (int)qtail : -1, nq1, Fn, [&](int w) {
+            for_level<W>(a, queued ? (int)qtail : -1, nq1, Fn, a.wq + (size_t)d * 8 + WQ_PULL, [&](int w) {
                 if (heavy(a, w)) return;
                 const Bits<W> t = load_bits<W>(Fn + (size_t)w * W);
                 const Bits<W> vold = load_bits<W>(a.vis + (size_t)w * W);
@@ -525,7 +559,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
                 gather<W, false>(a, __ldg(a.rp + w), __ldg(a.rp + w + 1), Fd, t, acc, facc, ovf);
                 settle<W>(a, w, vold, t, act, acc, nullptr, &bc);
             });
-            for_chunks(a, [&](int c, int h, int j0, int j1) {
+            for_chunks(a, a.wq + (size_t)d * 8 + WQ_PULL_C, [&](int c, int h, int j0, int j1) {
                 const Bits<W> t = load_bits<W>(Fn + (size_t)h * W);
                 if (!any_bits<W>(t)) return;
                 unsigned long long acc[2 * W];
@@ -614,7 +648,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
             part = dev::group_sum_ff<32>(part);
             if (lane == 0 && part.hi != 0.0f) a.scores[v] += dev::ff_to_double(part);
         };
-        for_level<W>(a, ql, nl, Fl, [&](int v) {
+        for_level<W>(a, ql, nl, Fl, a.wq + (size_t)l * 8 + WQ_BACK, [&](int v) {
             if (heavy(a, v)) return;
             const Bits<W> mv = load_bits<W>(Fl + (size_t)v * W);
             unsigned long long acc[2 * W];
@@ -625,7 +659,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
             gather<W, true>(a, __ldg(a.rp + v), __ldg(a.rp + v + 1), Fs, mv, acc, facc, dummy);
             finish(v, mv, facc);
         });
-        for_chunks(a, [&](int c, int h, int j0, int j1) {
+        for_chunks(a, a.wq + (size_t)l * 8 + WQ_BACK_C, [&](int c, int h, int j0, int j1) {
             const Bits<W> mv = load_bits<W>(Fl + (size_t)h * W);
             if (!any_bits<W>(mv)) return;
             unsigned long long acc[2 * W];
@@ -705,7 +739,7 @@ Layout layout(const nk_graph *g, int B, int lcap)
     L.off_queue = o;
     o = align_up(o + (size_t)L.qcap * 4);
     L.off_cnt = o;
-    o = align_up(o + (size_t)(lcap + 3) * (3 * 4 + 2 * 8));
+    o = align_up(o + (size_t)(lcap + 3) * (3 * 4 + 2 * 8 + 8 * 4));
     L.off_part = o;
     o = align_up(o + (size_t)chunk_count(g) * B * 8);
     L.total = o;
@@ -779,6 +813,7 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
         a.vcnt = reinterpret_cast<int32_t *>(a.dmu + lv);
         a.qcnt = a.vcnt + lv;
         a.qoff = a.qcnt + lv;
+        a.wq = a.qoff + lv;
         a.scores = d_scores;
         a.hv = g->heavy[0].as<int32_t>();
         a.hfirst = g->heavy[1].as<int32_t>();
