@@ -49,13 +49,14 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kErrDepth = 100;  // internal status: BFS deeper than the level slabs
+constexpr int kErrCheck = 101;  // internal status: a device-side range check failed
 constexpr int kStartLevels = 48; // level slabs of a first attempt
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kTraceCap = 1024;
 constexpr int kChunk = kHeavyChunk;  // arcs per work item; longer rows are split
 constexpr int kGrabQ = 8;            // queue entries a warp takes at a time
 constexpr int kGrabV = 64;           // vertices a warp scans at a time
-constexpr int kGrabC = 2;            // heavy chunks a warp takes at a time
+constexpr int kGrabCMax = 16;        // most heavy chunks a warp takes at a time
 // work-counter slots of a level
 enum { WQ_BU = 0, WQ_BU_C, WQ_PUSH, WQ_PUSH_C, WQ_PULL, WQ_PULL_C, WQ_BACK, WQ_BACK_C };
 
@@ -157,6 +158,16 @@ __device__ __forceinline__ void add_carry(unsigned long long &acc, unsigned &car
     asm("add.cc.u64 %0, %0, %2;\n\taddc.u32 %1, %1, 0;" : "+l"(acc), "+r"(carry) : "l"(x));
 }
 
+// Records the first failed device-side check (code, where, offending value); every CTA
+// then leaves at its next grid barrier and the host reports the status.
+__device__ __forceinline__ void check_failed(const BArgs &a, int code, int where, int value)
+{
+    if (atomicCAS(&a.ctrl->err, 0, code) == 0) {
+        a.ctrl->where = where;
+        a.ctrl->bad_id = value;
+    }
+}
+
 // For the warp's vertex with adjacency [beg, end): per source slot, the sum of sp over
 // the neighbours c whose Fsel[c] & tgt holds that source bit; uint64 sums (sigma, with
 // carry detection) or double-single sums (psi).  Lanes over neighbours find the relevant
@@ -172,6 +183,10 @@ __device__ __forceinline__ void gather(const BArgs &a, int beg, int end,
     const int lane = threadIdx.x & 31;
     const unsigned lanebit = 1u << lane;
     unsigned carry = 0;
+    if (beg < 0 || end < beg || (long long)end > a.A) {  // warp-uniform
+        if (lane == 0) check_failed(a, kErrCheck, 1, beg);
+        return;
+    }
     for (int base = beg; base < end; base += 32) {
         const int j = base + lane;
         int c = 0;
@@ -271,9 +286,11 @@ __device__ __forceinline__ void settle(const BArgs &a, int w, const Bits<W> &vol
 }
 
 // Calls fn(v) with the whole warp for every vertex of a level: the queued entries
-// queue[qo, qo+nq) or, if qo < 0, every v with Fl[v] != 0 (scanned 32 at a time).
+// queue[qo, qo+nq) or, if qo < 0, every v with Fl[v] != 0 (scanned 32 at a time; nq is
+// then the level's vertex count).
 // Calls fn(v) with the whole warp for every vertex of a level: the queued entries
-// queue[qo, qo+nq) or, if qo < 0, every v with Fl[v] != 0 (scanned 32 at a time).  Warps
+// queue[qo, qo+nq) or, if qo < 0, every v with Fl[v] != 0 (scanned 32 at a time; nq is
+// then the level's vertex count).  Warps
 // take work dynamically from the zeroed counter *ctr (8 entries or 64 vertices at a
 // time), so that power-law degrees do not leave a few warps finishing long after the
 // rest.
@@ -282,21 +299,54 @@ __device__ __forceinline__ void for_level(const BArgs &a, int qo, int nq,
                                           const unsigned long long *Fl, int32_t *ctr, Fn fn)
 {
     const int lane = threadIdx.x & 31;
+    // every loop below is also bounded in time: lane 0 checks the phase deadline once per
+    // grab or tile and the warp leaves together (the status is read at the next barrier)
+    const uint64_t deadline = dev::globaltimer() + a.limit_ns;
+    auto expired = [&]() {
+        int e = 0;
+        if (lane == 0 && dev::globaltimer() > deadline) {
+            check_failed(a, NK_ERR_TIMEOUT, 2, nq);
+            e = 1;
+        }
+        return __shfl_sync(FULL, e, 0) != 0;
+    };
     if (qo >= 0) {
         for (;;) {
             int i0 = 0;
             if (lane == 0) i0 = atomicAdd(ctr, kGrabQ);
             i0 = __shfl_sync(FULL, i0, 0);
-            if (i0 >= nq) break;
+            if (i0 >= nq || expired()) break;
             const int i1 = min(i0 + kGrabQ, nq);
-            for (int i = i0; i < i1; ++i) fn(__ldcg(a.queue + qo + i));
+            for (int i = i0; i < i1; ++i) {
+                const int v = __ldcg(a.queue + qo + i);
+                if ((unsigned)v >= (unsigned)a.n) {  // warp-uniform
+                    if (lane == 0) check_failed(a, kErrCheck, 3, v);
+                    continue;
+                }
+                fn(v);
+            }
+        }
+    } else if ((long long)nq * 32 < a.n) {
+        // a sparse level (fewer than n/32 vertices): a static scan, no counter traffic
+        const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+        for (long long base = wid * 32; base < a.n; base += nw * 32) {
+            if (expired()) break;
+            const long long v = base + lane;
+            const bool nz = v < a.n && any_bits<W>(load_bits<W>(Fl + (size_t)v * W));
+            unsigned m = __ballot_sync(FULL, nz);
+            while (m) {
+                const int t = __ffs(m) - 1;
+                m &= m - 1;
+                fn((int)(base + t));
+            }
         }
     } else {
         for (;;) {
             int t0 = 0;
             if (lane == 0) t0 = atomicAdd(ctr, kGrabV);
             t0 = __shfl_sync(FULL, t0, 0);
-            if (t0 >= a.n) break;
+            if (t0 >= a.n || expired()) break;
             for (int base = t0; base < min(t0 + kGrabV, a.n); base += 32) {
                 const int v = base + lane;
                 const bool nz = v < a.n && any_bits<W>(load_bits<W>(Fl + (size_t)v * W));
@@ -325,16 +375,28 @@ __device__ __forceinline__ void trace_mark(const BArgs &a, int &ti, int level, i
 }
 
 // Work on the chunks of heavy vertices: fn(c, h, j0, j1) per chunk, with the whole warp;
-// chunks are taken dynamically from the zeroed counter *ctr.
+// chunks are taken dynamically from the zeroed counter *ctr, and the loop is bounded in
+// time like the others.
 template <class Fn> __device__ __forceinline__ void for_chunks(const BArgs &a, int32_t *ctr, Fn fn)
 {
     const int lane = threadIdx.x & 31;
+    const uint64_t deadline = dev::globaltimer() + a.limit_ns;
+    // grab about C / (32 warps) chunks, 1..16: few chunks stay spread over many warps,
+    // millions of chunks cost few atomics
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int gc = (int)max(1LL, min((long long)kGrabCMax, (long long)a.C / (32 * nw)));
     for (;;) {
         int c0 = 0;
-        if (lane == 0) c0 = atomicAdd(ctr, kGrabC);
+        if (lane == 0) {
+            c0 = atomicAdd(ctr, gc);
+            if (c0 < a.C && dev::globaltimer() > deadline) {
+                check_failed(a, NK_ERR_TIMEOUT, 4, c0);
+                c0 = a.C;
+            }
+        }
         c0 = __shfl_sync(FULL, c0, 0);
         if (c0 >= a.C) break;
-        for (int c = c0; c < min(c0 + kGrabC, a.C); ++c) {
+        for (int c = c0; c < min(c0 + gc, a.C); ++c) {
             const int i = __ldg(a.chunk_h + c);
             const int h = __ldg(a.hv + i);
             const int j0 = __ldg(a.rp + h) + (c - __ldg(a.hfirst + i)) * kChunk;
@@ -456,8 +518,15 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
         if (use_bu) {
             // ---- bottom-up (a): light vertices with unvisited sources pull from level d;
             //      chunks of heavy vertices store partial sums
+            const uint64_t bu_deadline = dev::globaltimer() + a.limit_ns;
             for (int t0 = 0;;) {
-                if (lane == 0) t0 = atomicAdd(a.wq + (size_t)d * 8 + WQ_BU, 32);
+                if (lane == 0) {
+                    t0 = atomicAdd(a.wq + (size_t)d * 8 + WQ_BU, 32);
+                    if (t0 < a.n && dev::globaltimer() > bu_deadline) {
+                        check_failed(a, NK_ERR_TIMEOUT, 5, t0);
+                        t0 = a.n;
+                    }
+                }
                 t0 = __shfl_sync(FULL, t0, 0);
                 if (t0 >= a.n) break;
                 const long long base = t0;
@@ -628,7 +697,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
         const unsigned long long *Fl = a.F + (size_t)l * slab;
         const unsigned long long *Fs = a.F + (size_t)(l + 1) * slab;
         const int ql = __ldcg(a.qoff + l);
-        const int nl = ql >= 0 ? __ldcg(a.qcnt + l) : 0;
+        const int nl = ql >= 0 ? __ldcg(a.qcnt + l) : __ldcg(a.vcnt + l);
         // delta/psi/score of vertex v from its successor sums facc (whole warp)
         // psi_v = 1/sigma_v + acc and delta_v = sigma_v * acc (Brandes' recurrence with
         // sigma_v factored out), in double-single; the vertex's delta summed over its
@@ -877,7 +946,11 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
         std::vector<int> deep;
         for (int bi : todo) {
             if (h[bi].err == NK_ERR_TIMEOUT)
-                return set_error(NK_ERR_TIMEOUT, "batched sweep aborted: a bounded grid wait ran out");
+                return set_error(NK_ERR_TIMEOUT, "batched sweep aborted: a bounded device-side wait or phase ran out (check %d, value %d)",
+                                 h[bi].where, h[bi].bad_id);
+            if (h[bi].err == kErrCheck)
+                return set_error(NK_ERR_CUDA, "batched sweep aborted: device range check %d failed (value %d)",
+                                 h[bi].where, h[bi].bad_id);
             ovf |= h[bi].ovf != 0;
             if (h[bi].err == kErrDepth) deep.push_back(bi);
         }

@@ -77,7 +77,9 @@ struct Ctrl {
     int depth;   // deepest BFS level
     int td_levels;
     int bu_levels;
-    int pad;
+    int where;   // phase * 4096 + level of the first failed device-side check
+    int bad_id;  // offending value of that check
+    int pad[3];
 };
 
 // Tuned settings remembered per graph by the autotuner.
