@@ -57,7 +57,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--config", default="rmat18", choices=sorted(CONFIGS))
-    p.add_argument("--serve-requests", type=int, default=200)
+    p.add_argument("--serve-requests", type=int, default=2000)
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -245,6 +245,8 @@ def serving_load(nk, torch, n_req, seed=3):
         g.free()
     return {"requests": len(reqs), "capacity_req_per_s": cap, "arrival_rate_req_per_s": lam,
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+            "queue_p50_ms": st["queue_p50_ms"], "queue_p99_ms": st["queue_p99_ms"],
+            "run_p50_ms": st["run_p50_ms"], "run_p99_ms": st["run_p99_ms"],
             "gteps": st["edges_x_sources"] / wall / 1e9, "wall_s": wall,
             "peak_inflight": st["peak_inflight"], "peak_bytes": st["peak_bytes"],
             "closed_loop_gteps": st["edges_x_sources"] / closed_s / 1e9}

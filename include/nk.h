@@ -195,7 +195,8 @@ typedef int64_t nk_req;
 typedef struct nk_server_opts {
     double mem_budget_bytes; /* device bytes for per-request state; 0 = 60% of free */
     int32_t max_inflight;    /* requests on the GPU at once (streams); 0 = 8 */
-    int32_t batch;           /* sources per batch for served requests; 0 = 64 */
+    int32_t batch;           /* sources per launch for served requests (64/128/256);
+                                0 = by graph size: 256 up to 4M arcs, else 128 */
     double timeout_s;        /* bound on device-side waits; 0 = 10 s */
     int32_t reserved[8];
 } nk_server_opts;
@@ -207,6 +208,8 @@ typedef struct nk_server_stats {
     double edges_x_sources;          /* sum over completed requests of m * k */
     int64_t peak_inflight;
     double peak_bytes;
+    double queue_p50_ms, queue_p99_ms; /* submit-to-admission wait */
+    double run_p50_ms, run_p99_ms;     /* admission-to-completion time */
 } nk_server_stats;
 
 int nk_server_create(const nk_server_opts *opts, nk_server **out);

@@ -848,7 +848,8 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
     NK_TRY(ws[WS_BCTRL].ensure(sizeof(Ctrl) * nb));
     const int bps = blocks_per_sm<W>();
     if (bps < 1) return set_error(NK_ERR_CUDA, "batched kernel cannot be resident");
-    const int grid = std::max(1, bps * num_sms() / std::max(1, cfg.grid_div));
+    int grid = std::max(1, bps * num_sms() / std::max(1, cfg.grid_div));
+    if (cfg.grid_ctas > 0) grid = std::min(grid, cfg.grid_ctas);
     Ctrl *ctrls = ws[WS_BCTRL].as<Ctrl>();
     std::vector<int> todo(nb);
     for (int bi = 0; bi < nb; ++bi) todo[bi] = bi;

@@ -145,6 +145,7 @@ struct RunCfg {
     bool time_kernels = false;
     DevBuf *ws = nullptr;  // scratch slots (8); null = the graph's cached workspace
     int grid_div = 1;      // persistent grids use 1/grid_div of the co-resident CTAs
+    int grid_ctas = 0;     // if > 0: persistent grids use at most this many CTAs
     int lcap = 0;          // batched level slabs; 0 = sized from free memory
     uint64_t limit_ns = 0; // bound on device-side waits; 0 = the process-wide bound
 };

@@ -7,9 +7,11 @@
 // own non-blocking CUDA stream; its request's state (sampled sources, per-batch bitset
 // levels, sigma/psi rows, scores) is allocated stream-ordered on that stream and freed
 // when the request ends, so the work of different requests - on different graphs or on
-// the same one - overlaps on the device.  The persistent kernels of a slot use
-// 1/max_inflight of the co-resident CTAs, so that up to max_inflight of them are
-// resident together.  CSR arrays stay resident in the graph objects the caller owns.
+// the same one - overlaps on the device.  A request's persistent grid is sized by its
+// graph (about one CTA per 8192 arcs, at least 128, at most half of the co-resident
+// CTAs): small requests stay cheap to synchronise and many run side by side, large ones
+// get up to half of the GPU, so that a large request never holds the small ones back.  CSR arrays
+// stay resident in the graph objects the caller owns.
 //
 // Latency is measured from submit to the moment the scores are in the caller's buffer.
 #include <algorithm>
@@ -37,7 +39,7 @@ struct Request {
     int32_t k = 0;
     double *scores = nullptr;
     size_t need = 0;
-    clk::time_point t_submit, t_done;
+    clk::time_point t_submit, t_start, t_done;
     int state = 0;  // 0 queued, 1 running, 2 done
     int rc = NK_OK;
     std::string err;
@@ -51,7 +53,8 @@ constexpr int kServeLcap = 64;
 struct nk_server {
     nk_server_opts opts{};
     size_t budget = 0, used = 0, peak_bytes = 0;
-    int batch = 64, slots = 8;
+    int batch = 128, slots = 8;
+    bool batch_fixed = false;  // the caller fixed the batch width
     uint64_t limit_ns = 0;
     int device = 0;
     std::mutex mu;
@@ -66,11 +69,22 @@ struct nk_server {
     int64_t peak_inflight = 0;
     double busy_s = 0, exs = 0;
     nk::clk::time_point busy_since;
-    std::vector<double> lat_ms;
+    std::vector<double> lat_ms, wait_ms, run_ms;
 };
 
 namespace nk {
 namespace {
+
+// Sources per launch for a request: on graphs of up to 4M arcs a launch costs about the
+// same whatever its width (the level count and its synchronisation dominate), so small
+// requests take 256 sources per launch (one or few launches); larger graphs take the
+// server's batch width.  Never wider than k rounded up to 64.
+int request_batch(const nk_server *S, const nk_graph *g, int32_t k)
+{
+    int B = S->batch_fixed ? S->batch : (g->A <= (4ll << 20) ? 256 : 128);
+    while (B > 64 && (B >> 1) >= k) B >>= 1;
+    return B;
+}
 
 size_t request_bytes(const nk_graph *g, int B, int32_t k)
 {
@@ -95,9 +109,13 @@ int run_request(nk_server *S, Request *r, cudaStream_t st, double **h_buf, size_
     NK_CUDA(cudaMemsetAsync(dsc.p, 0, sizeof(double) * n, st));
     RunCfg cfg;
     cfg.mode = NK_MODE_BATCHED;
-    cfg.batch = S->batch;
+    cfg.batch = request_batch(S, g, r->k);
     cfg.ws = ws;
-    cfg.grid_div = S->slots;
+    // persistent grid sized by the graph: about one CTA per 8192 arcs, at least 128, at
+    // most half of the co-resident CTAs (co-residency is guaranteed per launch; launches
+    // that do not fit beside the running ones wait for their CTAs to free up)
+    cfg.grid_ctas = (int)std::min<int64_t>(std::max<int64_t>(g->A / 8192, 128), 1 << 20);
+    cfg.grid_div = 2;  // no request takes more than half of the co-resident CTAs
     cfg.lcap = std::min(kServeLcap, std::max(n, 4));
     cfg.limit_ns = S->limit_ns;
     NK_TRY(run_batched(g, dsrc.as<int32_t>(), r->k, dsc.as<double>(), cfg, nullptr, st));
@@ -134,7 +152,8 @@ void worker(nk_server *S)
             S->queue.pop_front();
             S->used += r->need;
             S->peak_bytes = std::max(S->peak_bytes, S->used);
-            if (S->running++ == 0) S->busy_since = clk::now();
+            r->t_start = clk::now();
+            if (S->running++ == 0) S->busy_since = r->t_start;
             S->peak_inflight = std::max<int64_t>(S->peak_inflight, S->running);
             r->state = 1;
         }
@@ -152,6 +171,8 @@ void worker(nk_server *S)
             if (rc == NK_OK) {
                 ++S->completed;
                 S->lat_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+                S->wait_ms.push_back(std::chrono::duration<double, std::milli>(r->t_start - r->t_submit).count());
+                S->run_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_start).count());
                 S->exs += (double)(r->g->A / 2) * (double)r->k;
             } else {
                 ++S->failed;
@@ -201,7 +222,8 @@ int nk_server_create(const nk_server_opts *opts, nk_server **out)
     NK_CUDA(cudaMemGetInfo(&free_b, &total_b));
     S->budget = o.mem_budget_bytes > 0 ? (size_t)o.mem_budget_bytes : (size_t)(0.6 * (double)free_b);
     S->slots = o.max_inflight > 0 ? o.max_inflight : 8;
-    S->batch = o.batch > 0 ? o.batch : 64;
+    S->batch = o.batch > 0 ? o.batch : 128;
+    S->batch_fixed = o.batch > 0;
     S->limit_ns = o.timeout_s > 0 ? (uint64_t)(o.timeout_s * 1e9) : 0;
     for (int i = 0; i < S->slots; ++i) S->workers.emplace_back(worker, S);
     *out = S;
@@ -235,7 +257,7 @@ int nk_serve_submit(nk_server *S, const nk_graph *gc, uint64_t seed, int32_t k, 
     r->seed = seed;
     r->k = k;
     r->scores = scores;
-    r->need = request_bytes(g, S->batch, k);
+    r->need = request_bytes(g, request_batch(S, g, k), k);
     {
         std::lock_guard<std::mutex> lk(S->mu);
         if (S->draining) {
@@ -306,6 +328,10 @@ int nk_server_get_stats(nk_server *S, nk_server_stats *out)
     out->edges_x_sources = S->exs;
     out->peak_inflight = S->peak_inflight;
     out->peak_bytes = (double)S->peak_bytes;
+    out->queue_p50_ms = pct(S->wait_ms, 50);
+    out->queue_p99_ms = pct(S->wait_ms, 99);
+    out->run_p50_ms = pct(S->run_ms, 50);
+    out->run_p99_ms = pct(S->run_ms, 99);
     return NK_OK;
 }
 

@@ -474,7 +474,9 @@ int run(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores, const Ru
     for (int32_t i = 0; i < k; ++i) {
         a.src = d_src + i;
         void *args[] = {&a};
-        NK_CUDA(cudaLaunchCooperativeKernel(L.fn, dim3(std::max(1, L.grid / std::max(1, cfg.grid_div))), dim3(kThreads), args, 0, s));
+        int grid = std::max(1, L.grid / std::max(1, cfg.grid_div));
+        if (cfg.grid_ctas > 0) grid = std::min(grid, cfg.grid_ctas);
+        NK_CUDA(cudaLaunchCooperativeKernel(L.fn, dim3(grid), dim3(kThreads), args, 0, s));
         ::nk::count_launch();
     }
     if (cfg.time_kernels) NK_CUDA(cudaEventRecord(e1, s));

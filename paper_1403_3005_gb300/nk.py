@@ -66,7 +66,9 @@ class ServerStats(ctypes.Structure):
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("max_ms", ctypes.c_double), ("busy_s", ctypes.c_double),
                 ("edges_x_sources", ctypes.c_double), ("peak_inflight", ctypes.c_int64),
-                ("peak_bytes", ctypes.c_double)]
+                ("peak_bytes", ctypes.c_double), ("queue_p50_ms", ctypes.c_double),
+                ("queue_p99_ms", ctypes.c_double), ("run_p50_ms", ctypes.c_double),
+                ("run_p99_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
