@@ -222,6 +222,7 @@ def serving_load(nk, torch, n_req, seed=3):
     for i in ids:
         assert srv.wait(i, 600.0) == 0
     closed_s = time.perf_counter() - t0
+    cst = srv.stats()
     srv.close()
     cap = len(reqs) / closed_s
     # open loop at 0.7 C
@@ -247,9 +248,12 @@ def serving_load(nk, torch, n_req, seed=3):
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
             "queue_p50_ms": st["queue_p50_ms"], "queue_p99_ms": st["queue_p99_ms"],
             "run_p50_ms": st["run_p50_ms"], "run_p99_ms": st["run_p99_ms"],
+            "launches": st["jobs"], "packed_requests": st["packed_requests"],
             "gteps": st["edges_x_sources"] / wall / 1e9, "wall_s": wall,
             "peak_inflight": st["peak_inflight"], "peak_bytes": st["peak_bytes"],
-            "closed_loop_gteps": st["edges_x_sources"] / closed_s / 1e9}
+            "closed_loop_gteps": cst["edges_x_sources"] / closed_s / 1e9,
+            "closed_loop_p50_ms": cst["p50_ms"], "closed_loop_p99_ms": cst["p99_ms"],
+            "closed_loop_launches": cst["jobs"], "closed_loop_packed_requests": cst["packed_requests"]}
 
 
 def cpu_baseline(cfg, seconds, rank_seed):

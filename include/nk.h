@@ -198,7 +198,8 @@ typedef struct nk_server_opts {
     int32_t batch;           /* sources per launch for served requests (64/128/256);
                                 0 = by graph size: 256 up to 4M arcs, else 128 */
     double timeout_s;        /* bound on device-side waits; 0 = 10 s */
-    int32_t reserved[8];
+    int32_t no_pack;         /* 1: never pack small requests into one launch */
+    int32_t reserved[7];
 } nk_server_opts;
 
 typedef struct nk_server_stats {
@@ -210,6 +211,8 @@ typedef struct nk_server_stats {
     double peak_bytes;
     double queue_p50_ms, queue_p99_ms; /* submit-to-admission wait */
     double run_p50_ms, run_p99_ms;     /* admission-to-completion time */
+    int64_t jobs;                      /* launches of work started (single or packed) */
+    int64_t packed_requests;           /* requests that ran inside a packed launch */
 } nk_server_stats;
 
 int nk_server_create(const nk_server_opts *opts, nk_server **out);
@@ -219,7 +222,10 @@ void nk_server_destroy(nk_server *srv);
 /* Queues a sampled-betweenness request (graph, seed, k).  `scores` (n doubles, host)
  * must stay valid until nk_serve_poll returns something other than NK_PENDING.
  * Admission is by the device-memory budget; requests larger than the whole budget are
- * rejected with NK_ERR_NOMEM. */
+ * rejected with NK_ERR_NOMEM.  Consecutive small requests (graphs of up to 4M arcs,
+ * k <= 128) are packed into one launch of up to 256 sources on the block-diagonal union
+ * of their graphs (BFS trees never cross graphs, so each request's scores are those of
+ * the request alone, up to FP summation order). */
 int nk_serve_submit(nk_server *srv, const nk_graph *g, uint64_t seed, int32_t k,
                     double *scores, nk_req *id);
 

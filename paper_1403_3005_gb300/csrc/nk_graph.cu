@@ -495,6 +495,8 @@ int build_heavy(nk_graph *g, cudaStream_t s)
     NK_CUDA(cudaStreamSynchronize(s));
     g->heavy_C = (int32_t)c;
     g->heavy_H = (int32_t)hv.size();
+    g->h_hv = std::move(hv);
+    g->h_hfirst = std::move(hfirst);
     return NK_OK;
 }
 

@@ -108,6 +108,7 @@ struct nk_graph {
     std::mutex heavy_mu;
     nk::DevBuf heavy[3];
     int32_t heavy_H = -1, heavy_C = 0;
+    std::vector<int32_t> h_hv, h_hfirst;  // host copies of heavy[0] and heavy[1]
 };
 
 namespace nk {

@@ -55,6 +55,7 @@ struct nk_server {
     size_t budget = 0, used = 0, peak_bytes = 0;
     int batch = 128, slots = 8;
     bool batch_fixed = false;  // the caller fixed the batch width
+    bool pack = true;          // pack consecutive small requests into one launch
     uint64_t limit_ns = 0;
     int device = 0;
     std::mutex mu;
@@ -67,6 +68,7 @@ struct nk_server {
     int64_t submitted = 0, completed = 0, failed = 0, rejected = 0;
     int running = 0;
     int64_t peak_inflight = 0;
+    int64_t launches_jobs = 0, packed = 0;  // jobs started; requests that ran in packs
     double busy_s = 0, exs = 0;
     nk::clk::time_point busy_since;
     std::vector<double> lat_ms, wait_ms, run_ms;
@@ -133,6 +135,147 @@ int run_request(nk_server *S, Request *r, cudaStream_t st, double **h_buf, size_
     return NK_OK;
 }
 
+// ---------------------------------------------------------------- packed launches
+// A request is small when its graph has at most 4M arcs and k <= 256; small requests
+// waiting in the queue (the first kPackLookahead entries, larger requests keep their
+// order) share launches of 256 sources, up to 1024 sources per pack, on the
+// block-diagonal union of their graphs: vertex ids of member r are shifted by the vertices of the members before it,
+// its sources by the same amount, so the BFS trees of different members never meet and
+// each member's slice of the union scores is its own result.
+constexpr int64_t kSmallArcs = 4ll << 20;
+constexpr int kPackWidth = 256;      // sources per launch of a pack
+constexpr int kPackSources = 1024;   // sources per pack (up to four launches)
+constexpr int kPackMembers = 32;
+constexpr int kPackLookahead = 64;   // queued requests a pack may pick from
+constexpr int64_t kPackVertices = 4ll << 20;
+
+bool small_request(const Request *r) { return r->g->A <= kSmallArcs && r->k <= 256; }
+
+__global__ void k_union_rows(const int32_t *rp, int32_t n, int64_t arc_off, int32_t *rp_u)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        rp_u[v] = (int32_t)(rp[v] + arc_off);
+}
+
+__global__ void k_union_cols(const int32_t *col, int64_t A, int32_t vert_off, int32_t *col_u)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < A;
+         j += (int64_t)gridDim.x * blockDim.x)
+        col_u[j] = col[j] + vert_off;
+}
+
+__global__ void k_shift(int32_t *p, int32_t count, int32_t by)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) p[i] += by;
+}
+
+__global__ void k_set_last(int32_t *rp_u, int32_t n_u, int32_t A_u) { rp_u[n_u] = A_u; }
+
+int blocks_for(int64_t items) { return (int)std::max<int64_t>(1, std::min<int64_t>((items + 255) / 256, 4 * num_sms())); }
+
+int run_pack(nk_server *S, const std::vector<Request *> &rs, cudaStream_t st, double **h_buf,
+             size_t *h_cap)
+{
+    // offsets of each member in the union: vertices, arcs, sources, heavy rows, chunks
+    std::vector<int64_t> voff, aoff, soff;
+    int64_t n_u = 0, A_u = 0, k_u = 0;
+    int32_t maxdeg = 0;
+    for (Request *r : rs) {
+        voff.push_back(n_u);
+        aoff.push_back(A_u);
+        soff.push_back(k_u);
+        n_u += r->g->n;
+        A_u += r->g->A;
+        k_u += r->k;
+        maxdeg = std::max(maxdeg, r->g->max_deg);
+    }
+    nk_graph u;
+    u.n = (int32_t)n_u;
+    u.A = A_u;
+    u.max_deg = maxdeg;
+    for (DevBuf *b : {&u.rp, &u.col, &u.heavy[0], &u.heavy[1], &u.heavy[2]}) {
+        b->stream_ordered = true;
+        b->st = st;
+    }
+    NK_TRY(u.rp.ensure(sizeof(int32_t) * (n_u + 1)));
+    NK_TRY(u.col.ensure(sizeof(int32_t) * (A_u + 1)));
+    std::vector<int32_t> hv, hfirst, chunk_h;
+    for (size_t i = 0; i < rs.size(); ++i) {
+        const nk_graph *g = rs[i]->g;
+        k_union_rows<<<blocks_for(g->n), 256, 0, st>>>(g->rp.as<int32_t>(), g->n, aoff[i],
+                                                        u.rp.as<int32_t>() + voff[i]);
+        ::nk::count_launch();
+        if (g->A > 0) {
+            k_union_cols<<<blocks_for(g->A), 256, 0, st>>>(g->col.as<int32_t>(), g->A, (int32_t)voff[i],
+                                                            u.col.as<int32_t>() + aoff[i]);
+            ::nk::count_launch();
+        }
+        const int32_t hoff = (int32_t)hv.size(), coff = hfirst.empty() ? 0 : hfirst.back();
+        if (!hfirst.empty()) hfirst.pop_back();
+        for (size_t h = 0; h < g->h_hv.size(); ++h) {
+            hv.push_back(g->h_hv[h] + (int32_t)voff[i]);
+            hfirst.push_back(g->h_hfirst[h] + coff);
+            for (int32_t c = g->h_hfirst[h]; c < g->h_hfirst[h + 1]; ++c) chunk_h.push_back(hoff + (int32_t)h);
+        }
+        hfirst.push_back(coff + (g->h_hfirst.empty() ? 0 : g->h_hfirst.back()));
+    }
+    if (hfirst.empty()) hfirst.push_back(0);
+    k_set_last<<<1, 1, 0, st>>>(u.rp.as<int32_t>(), (int32_t)n_u, (int32_t)A_u);
+    ::nk::count_launch();
+    NK_CUDA(cudaGetLastError());
+    NK_TRY(u.heavy[0].ensure(sizeof(int32_t) * std::max<size_t>(hv.size(), 1)));
+    NK_TRY(u.heavy[1].ensure(sizeof(int32_t) * hfirst.size()));
+    NK_TRY(u.heavy[2].ensure(sizeof(int32_t) * std::max<size_t>(chunk_h.size(), 1)));
+    if (!hv.empty()) {
+        NK_CUDA(cudaMemcpyAsync(u.heavy[0].p, hv.data(), sizeof(int32_t) * hv.size(), cudaMemcpyHostToDevice, st));
+        NK_CUDA(cudaMemcpyAsync(u.heavy[2].p, chunk_h.data(), sizeof(int32_t) * chunk_h.size(), cudaMemcpyHostToDevice, st));
+    }
+    NK_CUDA(cudaMemcpyAsync(u.heavy[1].p, hfirst.data(), sizeof(int32_t) * hfirst.size(), cudaMemcpyHostToDevice, st));
+    u.heavy_H = (int32_t)hv.size();
+    u.heavy_C = hfirst.back();
+    // sources: each member's own sample, shifted into the union's id range
+    Tmp dsrc, dsc;
+    NK_TRY(dsrc.alloc(sizeof(int32_t) * k_u, st));
+    NK_TRY(dsc.alloc(sizeof(double) * n_u, st));
+    for (size_t i = 0; i < rs.size(); ++i) {
+        int32_t *p = dsrc.as<int32_t>() + soff[i];
+        NK_TRY(sample_sources_device(rs[i]->g->n, rs[i]->seed, rs[i]->k, p, st));
+        k_shift<<<blocks_for(rs[i]->k), 256, 0, st>>>(p, rs[i]->k, (int32_t)voff[i]);
+        ::nk::count_launch();
+    }
+    NK_CUDA(cudaMemsetAsync(dsc.p, 0, sizeof(double) * n_u, st));
+    DevBuf ws[8];
+    for (auto &b : ws) {
+        b.stream_ordered = true;
+        b.st = st;
+    }
+    RunCfg cfg;
+    cfg.mode = NK_MODE_BATCHED;
+    cfg.batch = k_u > 128 ? kPackWidth : (k_u > 64 ? 128 : 64);
+    cfg.ws = ws;
+    cfg.grid_ctas = (int)std::min<int64_t>(std::max<int64_t>(A_u / 8192, 128), 1 << 20);
+    cfg.grid_div = 2;
+    cfg.lcap = std::min<int64_t>(kServeLcap, std::max<int64_t>(n_u, 4));
+    cfg.limit_ns = S->limit_ns;
+    NK_TRY(run_batched(&u, dsrc.as<int32_t>(), (int32_t)k_u, dsc.as<double>(), cfg, nullptr, st));
+    for (size_t i = 0; i < rs.size(); ++i)
+        NK_TRY(scale_vector(dsc.as<double>() + voff[i], rs[i]->g->n,
+                            (double)rs[i]->g->n / (2.0 * (double)rs[i]->k), st));
+    if (*h_cap < (size_t)n_u) {
+        if (*h_buf) cudaFreeHost(*h_buf);
+        *h_buf = nullptr;
+        *h_cap = 0;
+        NK_CUDA(cudaMallocHost(h_buf, sizeof(double) * n_u));
+        *h_cap = n_u;
+    }
+    NK_CUDA(cudaMemcpyAsync(*h_buf, dsc.p, sizeof(double) * n_u, cudaMemcpyDeviceToHost, st));
+    NK_CUDA(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < rs.size(); ++i)
+        std::copy(*h_buf + voff[i], *h_buf + voff[i] + rs[i]->g->n, rs[i]->scores);
+    return NK_OK;
+}
+
 void worker(nk_server *S)
 {
     cudaSetDevice(S->device);
@@ -141,43 +284,77 @@ void worker(nk_server *S)
     double *h_buf = nullptr;
     size_t h_cap = 0;
     for (;;) {
-        Request *r = nullptr;
+        std::vector<Request *> job;
+        size_t need = 0;
         {
             std::unique_lock<std::mutex> lk(S->mu);
             S->cv_work.wait(lk, [&] {
                 return S->stop || (!S->queue.empty() && S->used + S->queue.front()->need <= S->budget);
             });
             if (S->stop) break;
-            r = S->queue.front();
+            job.push_back(S->queue.front());
             S->queue.pop_front();
-            S->used += r->need;
+            need = job[0]->need;
+            // pack the small requests that follow, in arrival order, while they fit
+            // (a pack runs 256 sources wide: its members' bytes are counted at that width)
+            if (S->pack && small_request(job[0])) {
+                int64_t k = job[0]->k, nv = job[0]->g->n;
+                size_t pneed = request_bytes(job[0]->g, kPackWidth, job[0]->k);
+                int looked = 0;
+                for (auto it = S->queue.begin(); it != S->queue.end() && looked < kPackLookahead &&
+                                                 (int)job.size() < kPackMembers;
+                     ++looked) {
+                    Request *q = *it;
+                    const size_t qneed = request_bytes(q->g, kPackWidth, q->k);
+                    if (!small_request(q) || k + q->k > kPackSources || nv + q->g->n > kPackVertices ||
+                        S->used + pneed + qneed > S->budget) {
+                        ++it;
+                        continue;
+                    }
+                    job.push_back(q);
+                    it = S->queue.erase(it);
+                    k += q->k;
+                    nv += q->g->n;
+                    pneed += qneed;
+                }
+                if (job.size() > 1) need = pneed;
+            }
+            S->used += need;
             S->peak_bytes = std::max(S->peak_bytes, S->used);
-            r->t_start = clk::now();
-            if (S->running++ == 0) S->busy_since = r->t_start;
+            const auto now = clk::now();
+            if (S->running++ == 0) S->busy_since = now;
             S->peak_inflight = std::max<int64_t>(S->peak_inflight, S->running);
-            r->state = 1;
+            for (Request *r : job) {
+                r->t_start = now;
+                r->state = 1;
+            }
+            ++S->launches_jobs;
+            if (job.size() > 1) S->packed += (int64_t)job.size();
         }
-        const int rc = run_request(S, r, st, &h_buf, &h_cap);
+        const int rc = job.size() == 1 ? run_request(S, job[0], st, &h_buf, &h_cap)
+                                       : run_pack(S, job, st, &h_buf, &h_cap);
         const std::string msg = rc == NK_OK ? std::string() : std::string(nk_last_error());
         {
             std::lock_guard<std::mutex> lk(S->mu);
-            r->t_done = clk::now();
-            r->rc = rc;
-            r->err = msg;
-            r->state = 2;
-            S->used -= r->need;
-            if (--S->running == 0)
-                S->busy_s += std::chrono::duration<double>(r->t_done - S->busy_since).count();
-            if (rc == NK_OK) {
-                ++S->completed;
-                S->lat_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
-                S->wait_ms.push_back(std::chrono::duration<double, std::milli>(r->t_start - r->t_submit).count());
-                S->run_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_start).count());
-                S->exs += (double)(r->g->A / 2) * (double)r->k;
-            } else {
-                ++S->failed;
+            const auto done = clk::now();
+            S->used -= need;
+            if (--S->running == 0) S->busy_s += std::chrono::duration<double>(done - S->busy_since).count();
+            for (Request *r : job) {
+                r->t_done = done;
+                r->rc = rc;
+                r->err = msg;
+                r->state = 2;
+                if (rc == NK_OK) {
+                    ++S->completed;
+                    S->lat_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count());
+                    S->wait_ms.push_back(std::chrono::duration<double, std::milli>(r->t_start - r->t_submit).count());
+                    S->run_ms.push_back(std::chrono::duration<double, std::milli>(r->t_done - r->t_start).count());
+                    S->exs += (double)(r->g->A / 2) * (double)r->k;
+                } else {
+                    ++S->failed;
+                }
+                r->g->pending.fetch_sub(1);
             }
-            r->g->pending.fetch_sub(1);
         }
         S->cv_done.notify_all();
         S->cv_work.notify_all();
@@ -224,6 +401,7 @@ int nk_server_create(const nk_server_opts *opts, nk_server **out)
     S->slots = o.max_inflight > 0 ? o.max_inflight : 8;
     S->batch = o.batch > 0 ? o.batch : 128;
     S->batch_fixed = o.batch > 0;
+    S->pack = o.no_pack == 0;
     S->limit_ns = o.timeout_s > 0 ? (uint64_t)(o.timeout_s * 1e9) : 0;
     for (int i = 0; i < S->slots; ++i) S->workers.emplace_back(worker, S);
     *out = S;
@@ -332,6 +510,8 @@ int nk_server_get_stats(nk_server *S, nk_server_stats *out)
     out->queue_p99_ms = pct(S->wait_ms, 99);
     out->run_p50_ms = pct(S->run_ms, 50);
     out->run_p99_ms = pct(S->run_ms, 99);
+    out->jobs = S->launches_jobs;
+    out->packed_requests = S->packed;
     return NK_OK;
 }
 

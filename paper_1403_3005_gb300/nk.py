@@ -57,7 +57,7 @@ class RunStats(ctypes.Structure):
 class ServerOpts(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_double), ("max_inflight", ctypes.c_int32),
                 ("batch", ctypes.c_int32), ("timeout_s", ctypes.c_double),
-                ("reserved", ctypes.c_int32 * 8)]
+                ("no_pack", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
 class ServerStats(ctypes.Structure):
@@ -68,7 +68,8 @@ class ServerStats(ctypes.Structure):
                 ("edges_x_sources", ctypes.c_double), ("peak_inflight", ctypes.c_int64),
                 ("peak_bytes", ctypes.c_double), ("queue_p50_ms", ctypes.c_double),
                 ("queue_p99_ms", ctypes.c_double), ("run_p50_ms", ctypes.c_double),
-                ("run_p99_ms", ctypes.c_double)]
+                ("run_p99_ms", ctypes.c_double), ("jobs", ctypes.c_int64),
+                ("packed_requests", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -339,10 +340,11 @@ def autotune(g: Graph, seed: int, k: int) -> RunOpts:
 class Server:
     """Continuous-batching betweenness server (nk_server_*)."""
 
-    def __init__(self, mem_budget_bytes=0.0, max_inflight=0, batch=0, timeout_s=0.0):
+    def __init__(self, mem_budget_bytes=0.0, max_inflight=0, batch=0, timeout_s=0.0, pack=True):
         o = ServerOpts()
         o.mem_budget_bytes, o.max_inflight, o.batch, o.timeout_s = (
             mem_budget_bytes, max_inflight, batch, timeout_s)
+        o.no_pack = 0 if pack else 1
         h = ctypes.c_void_p()
         _check(lib().nk_server_create(ctypes.byref(o), ctypes.byref(h)))
         self._h = h

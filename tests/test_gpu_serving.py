@@ -53,15 +53,44 @@ def test_mixed_load_equals_alone_and_oracle(nk):
             assert np.allclose(out, oracle.betweenness_sampled(rp, col, seed, k), rtol=RTOL, atol=ATOL)
 
 
+def test_small_requests_packed_into_one_launch(nk):
+    # many small requests on different graphs (and the same graph twice), k <= 128:
+    # packed launches on the union of their graphs; each result equals the request alone
+    # and the oracle
+    specs = [("er", 900, 31, dict(avg_deg=6.0), 40), ("ba", 2000, 32, dict(m0=3), 100),
+             ("rmat", 10, 33, {}, 64), ("er", 300, 34, dict(avg_deg=4.0), 7),
+             ("ba", 5000, 35, dict(m0=4), 128), ("rmat", 12, 36, {}, 90)]
+    graphs = [(nk.graph_generate(kd, sz, sd, **p), oracle.generate(kd, sz, sd, **p), k)
+              for kd, sz, sd, p, k in specs]
+    for pack in (True, False):
+        srv = nk.Server(max_inflight=1, pack=pack)   # one slot: the queue forms packs
+        reqs = []
+        for rep in range(2):
+            for i, (g, _, k) in enumerate(graphs):
+                rid, out = srv.submit(g, 7 + rep, k)
+                reqs.append((rid, out, i, 7 + rep))
+        for rid, out, i, seed in reqs:
+            assert srv.wait(rid, 300.0) == nk.OK
+        st = srv.stats()
+        srv.close()
+        if pack:
+            assert st["packed_requests"] >= 2 and st["jobs"] < len(reqs), st
+        else:
+            assert st["packed_requests"] == 0 and st["jobs"] == len(reqs), st
+        for rid, out, i, seed in reqs:
+            g, (n, rp, col), k = graphs[i]
+            assert np.allclose(out, oracle.betweenness_sampled(rp, col, seed, k), rtol=RTOL, atol=ATOL), (pack, i)
+
+
 def test_admission_by_budget_and_rejection(nk):
     g = nk.graph_generate("rmat", 14, 3)
-    probe = nk.Server(max_inflight=1)
+    probe = nk.Server(max_inflight=1, pack=False)
     assert probe.wait(probe.submit(g, 0, 100)[0], 300.0) == nk.OK
     need = probe.stats()["peak_bytes"]          # device bytes admitted for one request
     probe.close()
     assert need > 0
     # a budget that holds one request at a time: requests queue, then all finish
-    srv = nk.Server(mem_budget_bytes=1.5 * need, max_inflight=4)
+    srv = nk.Server(mem_budget_bytes=1.5 * need, max_inflight=4, pack=False)
     ids = [srv.submit(g, s, 100)[0] for s in range(5)]
     for i in ids:
         assert srv.wait(i, 300.0) == nk.OK
