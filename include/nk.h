@@ -140,6 +140,12 @@ int nk_sssp_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col, int64
 
 #define NK_RUN_DEVICE_PTRS 1u  /* scores (and src) are device pointers */
 #define NK_RUN_TIME_KERNELS 2u /* record per-launch durations of the sweep kernel */
+#define NK_RUN_CUDA_GRAPH 4u   /* sampled, batched, device pointers: capture the whole call
+                                  (sampler, persistent launches, scaling) into a CUDA graph
+                                  on first use and replay it for later calls with the same
+                                  graph, seed, k, options and output pointer; every replay
+                                  re-executes all kernels.  Falls back to the regular path
+                                  when a BFS is deeper than the captured level slabs. */
 
 typedef struct nk_run_opts {
     int32_t mode;      /* NK_MODE_* */

@@ -972,6 +972,91 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
     }
 }
 
+// Capturable form of one pass of launch_batches: no host synchronisation and no
+// allocation once prepared.  With prepare_only it sizes and allocates the workspace (call
+// it before a stream capture); otherwise it enqueues the status reset and the cooperative
+// launches (cudaLaunchKernelExC with the cooperative attribute, which stream capture
+// records as kernel nodes) and returns the per-batch status words for the caller to read.
+template <int W>
+int enqueue_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores,
+                    const RunCfg &cfg, cudaStream_t s, bool prepare_only, Ctrl **ctrls_out, int *nb_out)
+{
+    constexpr int B = 64 * W;
+    DevBuf *ws = scratch(cfg, g);
+    const int lcap = cfg.lcap > 0 ? std::min(cfg.lcap, std::max(g->n, 4)) : std::min(choose_lcap(g, B, ws), std::max(kStartLevels, 4));
+    if (lcap < 4) return set_error(NK_ERR_NOMEM, "not enough device memory for a batch of %d sources", B);
+    const int nb = (k + B - 1) / B;
+    const Layout L = layout(g, B, lcap);
+    if (prepare_only) {
+        NK_TRY(build_heavy(g, s));
+        NK_TRY(ws[WS_BATCH].ensure(L.total));
+        NK_TRY(ws[WS_BCTRL].ensure(sizeof(Ctrl) * nb));
+        if (blocks_per_sm<W>() < 1) return set_error(NK_ERR_CUDA, "batched kernel cannot be resident");
+        return NK_OK;
+    }
+    if (ws[WS_BATCH].bytes < L.total || ws[WS_BCTRL].bytes < sizeof(Ctrl) * nb)
+        return set_error(NK_ERR_ARG, "batched workspace not prepared");
+    const int bps = blocks_per_sm<W>();
+    if (bps < 1) return set_error(NK_ERR_CUDA, "batched kernel cannot be resident");
+    int grid = std::max(1, bps * num_sms() / std::max(1, cfg.grid_div));
+    if (cfg.grid_ctas > 0) grid = std::min(grid, cfg.grid_ctas);
+    char *base = ws[WS_BATCH].as<char>();
+    BArgs a;
+    a.n = g->n;
+    a.A = g->A;
+    a.rp = g->rp.as<int32_t>();
+    a.col = g->col.as<int32_t>();
+    a.lcap = lcap;
+    a.F = reinterpret_cast<unsigned long long *>(base + L.off_F);
+    a.vis = reinterpret_cast<unsigned long long *>(base + L.off_vis);
+    a.sp = reinterpret_cast<unsigned long long *>(base + L.off_sp);
+    a.qmark = reinterpret_cast<int32_t *>(base + L.off_qmark);
+    a.queue = reinterpret_cast<int32_t *>(base + L.off_queue);
+    a.qcap = L.qcap;
+    const size_t lv = (size_t)lcap + 3;
+    char *cb = base + L.off_cnt;
+    a.mfv = reinterpret_cast<unsigned long long *>(cb);
+    a.dmu = a.mfv + lv;
+    a.vcnt = reinterpret_cast<int32_t *>(a.dmu + lv);
+    a.qcnt = a.vcnt + lv;
+    a.qoff = a.qcnt + lv;
+    a.wq = a.qoff + lv;
+    a.scores = d_scores;
+    a.hv = g->heavy[0].as<int32_t>();
+    a.hfirst = g->heavy[1].as<int32_t>();
+    a.chunk_h = g->heavy[2].as<int32_t>();
+    a.H = g->heavy_H;
+    a.C = g->heavy_C;
+    a.part = reinterpret_cast<unsigned long long *>(base + L.off_part);
+    a.trace = nullptr;
+    a.limit_ns = cfg.limit_ns ? cfg.limit_ns : wait_limit_ns();
+    a.alpha = cfg.alpha > 0 ? cfg.alpha : 1.0;
+    a.dir = cfg.direction;
+    Ctrl *ctrls = ws[WS_BCTRL].as<Ctrl>();
+    NK_CUDA(cudaMemsetAsync(ctrls, 0, sizeof(Ctrl) * nb, s));
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeCooperative;
+    attr.val.cooperative = 1;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(grid);
+    lc.blockDim = dim3(kThreads);
+    lc.dynamicSmemBytes = 0;
+    lc.stream = s;
+    lc.attrs = &attr;
+    lc.numAttrs = 1;
+    for (int bi = 0; bi < nb; ++bi) {
+        a.src = d_src + (size_t)bi * B;
+        a.nsrc = std::min(B, k - bi * B);
+        a.ctrl = ctrls + bi;
+        void *args[] = {&a};
+        NK_CUDA(cudaLaunchKernelExC(&lc, (const void *)k_batch<W>, args));
+        ::nk::count_launch();
+    }
+    *ctrls_out = ctrls;
+    *nb_out = nb;
+    return NK_OK;
+}
+
 }  // namespace
 
 size_t batched_bytes(const nk_graph *g, int B) { return layout(g, B, 16).total; }
@@ -987,6 +1072,19 @@ int run_batched(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores,
     case 64: return launch_batches<1>(g, d_src, k, d_scores, cfg, st, s);
     case 128: return launch_batches<2>(g, d_src, k, d_scores, cfg, st, s);
     case 256: return launch_batches<4>(g, d_src, k, d_scores, cfg, st, s);
+    default: return set_error(NK_ERR_ARG, "batch must be 64, 128 or 256 (got %d)", B);
+    }
+}
+
+int enqueue_batched(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores,
+                    const RunCfg &cfg, cudaStream_t s, bool prepare_only, Ctrl **ctrls, int *nb)
+{
+    int B = cfg.batch;
+    if (B == 0) B = g->tuned.valid ? g->tuned.batch : 64;
+    switch (B) {
+    case 64: return enqueue_batches<1>(g, d_src, k, d_scores, cfg, s, prepare_only, ctrls, nb);
+    case 128: return enqueue_batches<2>(g, d_src, k, d_scores, cfg, s, prepare_only, ctrls, nb);
+    case 256: return enqueue_batches<4>(g, d_src, k, d_scores, cfg, s, prepare_only, ctrls, nb);
     default: return set_error(NK_ERR_ARG, "batch must be 64, 128 or 256 (got %d)", B);
     }
 }

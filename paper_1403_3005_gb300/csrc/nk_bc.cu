@@ -78,6 +78,109 @@ int run_device(nk_graph *g, const int32_t *d_src, int32_t k, double scale, doubl
     return scale_vector(d_scores, g->n, scale, s);
 }
 
+// Sampled, batched, device-pointer call through a captured CUDA graph (NK_RUN_CUDA_GRAPH).
+// Returns NK_PENDING when the captured run cannot give the result (a BFS deeper than its
+// level slabs): the caller then takes the regular path.
+int run_captured(nk_graph *g, uint64_t seed, int32_t k, double scale, double *d_scores,
+                 RunCfg cfg, cudaStream_t caller)
+{
+    // the legacy default stream cannot be captured: work on a private stream of this
+    // thread instead, after the caller's stream has drained (the call is synchronous)
+    thread_local cudaStream_t own = nullptr;
+    cudaStream_t s = caller;
+    if (caller == nullptr || caller == cudaStreamLegacy || caller == cudaStreamPerThread) {
+        if (!own) NK_CUDA(cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking));
+        NK_CUDA(cudaStreamSynchronize(caller));
+        s = own;
+    }
+    CapturedRun &e = g->captured;
+    if (cfg.batch == 0) cfg.batch = g->tuned.valid ? g->tuned.batch : 64;
+    if (cfg.alpha <= 0) cfg.alpha = 1.0;
+    cfg.ws = e.ws;
+    const bool hit = e.valid && e.seed == seed && e.k == k && e.batch == cfg.batch &&
+                     e.alpha == cfg.alpha && e.dir == cfg.direction && e.scores == d_scores &&
+                     e.scale == scale;
+    if (!hit) {
+        e.reset();
+        NK_TRY(e.src.ensure(sizeof(int32_t) * k));
+        Ctrl *ctrls = nullptr;
+        int nb = 0;
+        NK_TRY(enqueue_batched(g, e.src.as<int32_t>(), k, d_scores, cfg, s, true, &ctrls, &nb));
+        const int nbatch = (k + cfg.batch - 1) / cfg.batch;
+        NK_CUDA(cudaMallocHost(&e.h_status, sizeof(Ctrl) * nbatch));
+        NK_CUDA(cudaStreamSynchronize(s));
+        const uint64_t l0 = g_launches.load();
+        cudaGraph_t graph = nullptr;
+        NK_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        int rc = NK_OK;
+        do {
+            if (cudaMemsetAsync(d_scores, 0, sizeof(double) * g->n, s) != cudaSuccess) { rc = set_error(NK_ERR_CUDA, "memset in capture"); break; }
+            if ((rc = sample_sources_device(g->n, seed, k, e.src.as<int32_t>(), s)) != NK_OK) break;
+            if ((rc = enqueue_batched(g, e.src.as<int32_t>(), k, d_scores, cfg, s, false, &ctrls, &nb)) != NK_OK) break;
+            if ((rc = scale_vector(d_scores, g->n, scale, s)) != NK_OK) break;
+            if (cudaMemcpyAsync(e.h_status, ctrls, sizeof(Ctrl) * nb, cudaMemcpyDeviceToHost, s) != cudaSuccess) { rc = set_error(NK_ERR_CUDA, "status copy in capture"); break; }
+        } while (false);
+        const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        const uint64_t captured = g_launches.load() - l0;
+        g_launches.fetch_sub(captured);  // recorded, not run
+        if (rc != NK_OK || ce != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return rc != NK_OK ? rc : set_error(NK_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(ce));
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+            e.exec = nullptr;
+            return set_error(NK_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(ie));
+        }
+        e.valid = true;
+        e.seed = seed;
+        e.k = k;
+        e.batch = cfg.batch;
+        e.alpha = cfg.alpha;
+        e.dir = cfg.direction;
+        e.scores = d_scores;
+        e.scale = scale;
+        e.nb = nb;
+        e.launches = captured;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cfg.time_kernels) {
+        NK_CUDA(cudaEventCreate(&e0));
+        NK_CUDA(cudaEventCreate(&e1));
+        NK_CUDA(cudaEventRecord(e0, s));
+    }
+    NK_CUDA(cudaGraphLaunch(e.exec, s));
+    if (cfg.time_kernels) NK_CUDA(cudaEventRecord(e1, s));
+    NK_CUDA(cudaStreamSynchronize(s));
+    g_launches.fetch_add(e.launches);
+    t_stats = RunStats();
+    t_stats.mode = NK_MODE_BATCHED;
+    t_stats.batch = e.batch;
+    t_stats.tpv = 32;
+    t_stats.launches = e.nb;
+    t_stats.alpha = e.alpha;
+    if (cfg.time_kernels) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        t_stats.kernel_ms = ms;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    bool deep = false;
+    for (int i = 0; i < e.nb; ++i) {
+        const Ctrl &c = e.h_status[i];
+        if (c.err == NK_ERR_TIMEOUT) return set_error(NK_ERR_TIMEOUT, "captured sweep aborted: a bounded device-side wait ran out");
+        if (c.ovf) return set_error(NK_ERR_OVERFLOW, "a shortest-path count exceeded 2^64 - 1");
+        if (c.err != 0) deep = true;
+        t_stats.max_depth = std::max(t_stats.max_depth, c.depth);
+        t_stats.td_levels += c.td_levels;
+        t_stats.bu_levels += c.bu_levels;
+    }
+    return deep ? NK_PENDING : NK_OK;
+}
+
 // Common path of every betweenness entry point.  src == nullptr means "all vertices";
 // sample_k > 0 means "sample_k sources from sample_seed".
 int bc_entry(const nk_graph *gc, const int32_t *src, int32_t k, bool sample, uint64_t seed,
@@ -93,6 +196,10 @@ int bc_entry(const nk_graph *gc, const int32_t *src, int32_t k, bool sample, uin
     const bool dev = opts && (opts->flags & NK_RUN_DEVICE_PTRS);
     cudaStream_t s = stream();
     std::lock_guard<std::mutex> lock(g->mu);
+    if (sample && dev && (opts->flags & NK_RUN_CUDA_GRAPH) && cfg.mode != NK_MODE_PER_SOURCE) {
+        const int rc = run_captured(g, seed, k, scale, scores, cfg, s);
+        if (rc != NK_PENDING) return rc;  // NK_PENDING: deeper than the captured slabs
+    }
     Tmp dsrc, dscores, flag;
     const int32_t *d_src = nullptr;
     if (sample) {

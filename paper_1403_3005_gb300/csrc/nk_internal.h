@@ -82,6 +82,32 @@ struct Ctrl {
     int pad[3];
 };
 
+// A betweenness call captured into a CUDA graph (sampler, persistent launches, scaling,
+// status copy) with the scratch it owns, replayed by later identical calls.
+struct CapturedRun {
+    bool valid = false;
+    uint64_t seed = 0;
+    int32_t k = 0;
+    int batch = 0, dir = 0;
+    double alpha = 0, scale = 0;
+    double *scores = nullptr;
+    DevBuf ws[8];
+    DevBuf src;
+    Ctrl *h_status = nullptr;  // pinned copy of the per-batch status words
+    int nb = 0;
+    uint64_t launches = 0;     // kernels one replay runs
+    cudaGraphExec_t exec = nullptr;
+    void reset()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        if (h_status) cudaFreeHost(h_status);
+        h_status = nullptr;
+        valid = false;
+    }
+    ~CapturedRun() { reset(); }
+};
+
 // Tuned settings remembered per graph by the autotuner.
 struct Tuned {
     bool valid = false;
@@ -109,6 +135,7 @@ struct nk_graph {
     nk::DevBuf heavy[3];
     int32_t heavy_H = -1, heavy_C = 0;
     std::vector<int32_t> h_hv, h_hfirst;  // host copies of heavy[0] and heavy[1]
+    nk::CapturedRun captured;             // last call captured with NK_RUN_CUDA_GRAPH
 };
 
 namespace nk {
@@ -170,6 +197,12 @@ int run_sssp(nk_graph *g, int32_t src, int32_t *d_dist, uint64_t *d_sigma, cudaS
 // batch whose BFS is deeper than the level cap are re-run by the per-source form.
 int run_batched(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores,
                 const RunCfg &cfg, RunStats *st, cudaStream_t s);
+
+// Capturable pieces of the batched form: prepare_only sizes and allocates the scratch
+// (outside any stream capture); otherwise the status reset and the launches are enqueued
+// without host synchronisation, and *ctrls / *nb give the per-batch status words.
+int enqueue_batched(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores,
+                    const RunCfg &cfg, cudaStream_t s, bool prepare_only, Ctrl **ctrls, int *nb);
 
 // Device bytes the batched form needs for one batch of B sources on this graph.
 size_t batched_bytes(const nk_graph *g, int B);

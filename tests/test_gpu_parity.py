@@ -276,3 +276,24 @@ def test_autotune_then_run(nk):
     best = nk.autotune(g, 2, 300)
     assert best.batch in (64, 128, 256) and best.alpha > 0
     assert close(nk.betweenness_sampled(g, 2, 300), oracle.betweenness_sampled(rp, col, 2, 300))
+
+
+def test_cuda_graph_capture_and_replay(nk):
+    # NK_RUN_CUDA_GRAPH: the first call captures, later identical calls replay; every
+    # replay recomputes the same result, a changed seed recaptures; kernels are counted
+    import torch
+    g = nk.graph_generate("rmat", 13, 8)
+    n, rp, col = oracle.generate("rmat", 13, 8)
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    flags = nk.RUN_CUDA_GRAPH
+    for seed in (3, 3, 4, 4, 3):
+        out.fill_(-1.0)
+        l0 = nk.launch_count()
+        nk.betweenness_sampled(g, seed, 300, nk.run_opts(mode=2, batch=128, flags=flags), out=out)
+        assert nk.launch_count() > l0
+        assert close(out.cpu().numpy(), oracle.betweenness_sampled(rp, col, seed, 300)), seed
+    # a graph deeper than the captured level slabs falls back to the regular path
+    gp, rpp, colp = both(nk, G.path(400))
+    outp = torch.empty(400, dtype=torch.float64, device="cuda")
+    nk.betweenness_sampled(gp, 2, 100, nk.run_opts(mode=2, batch=64, flags=flags), out=outp)
+    assert close(outp.cpu().numpy(), oracle.betweenness_sampled(rpp, colp, 2, 100))
