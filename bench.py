@@ -149,9 +149,11 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ helpers
 def algorithmic_bytes_per_launch(n, A, B):
-    """Batched form, per launch of B sources: the CSR streamed once per sweep
-    (2 sweeps x (4A + 4n)), the per-level bitsets 24n ... in the per-source figure
-    (8A + 24n)/B + 34n of the hot-path byte model, times the B sources of a launch."""
+    """Algorithmic bytes of one launch of the batched form (B sources): per source
+    (8A + 24n)/B + 34n - the CSR (4A column ids + 4n row offsets) streamed once in each of
+    the two sweeps and 8n more bytes of per-vertex words, all shared by the B sources, plus
+    34n bytes of per-(vertex, source) state (sigma/psi written once and read once in each
+    sweep, 2 x 16n, and the level bits) - times B."""
     return (8.0 * A + 24.0 * n) + 34.0 * n * B
 
 
