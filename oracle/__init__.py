@@ -6,7 +6,8 @@ this package, and this package never imports the product library.
 
 Every function mirrors one C function and cites the passage of the paper it follows:
 Brandes' algorithm and the sampled estimate (Section 3.2, Table 1), BFS for unweighted
-graphs (Section 3.4), the generators of Section 5 (Table 2).
+graphs (Section 3.4), closeness exact and sampled (Table 1), the generators of Section 5
+(Table 2).
 """
 from __future__ import annotations
 
@@ -66,6 +67,7 @@ def _load():
             "or_betweenness": (ctypes.c_int, [i32, P, P, i32, P, dbl, P]),
             "or_betweenness_exact": (ctypes.c_int, [i32, P, P, P]),
             "or_betweenness_sampled": (ctypes.c_int, [i32, P, P, u64, i32, P]),
+            "or_closeness": (ctypes.c_int, [i32, P, P, i32, P, dbl, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -214,3 +216,27 @@ def betweenness_sampled(rp, col, seed: int, k: int) -> np.ndarray:
     if rc:
         raise OracleError(rc, "betweenness_sampled")
     return out
+
+
+# ---------------------------------------------------------------- closeness (Table 1)
+def closeness_sources(rp, col, src, scale: float):
+    """(far, reach): scale * sum of d(s, v), and scale * count, over sources s != v
+    that reach v."""
+    rp, col, src = _i32(rp), _i32(col), _i32(src)
+    n = len(rp) - 1
+    far = np.empty(n, np.float64)
+    reach = np.empty(n, np.float64)
+    rc = _load().or_closeness(n, _p(rp), _p(col), len(src), _p(src), scale, _p(far), _p(reach))
+    if rc:
+        raise OracleError(rc, "closeness")
+    return far, reach
+
+
+def closeness_exact(rp, col):
+    n = len(rp) - 1
+    return closeness_sources(rp, col, np.arange(n, dtype=np.int32), 1.0)
+
+
+def closeness_sampled(rp, col, seed: int, k: int):
+    n = len(rp) - 1
+    return closeness_sources(rp, col, sample_sources(n, seed, k), n / k)

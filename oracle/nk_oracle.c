@@ -444,3 +444,48 @@ int or_betweenness_sampled(int32_t n, const int32_t *row_ptr, const int32_t *col
     free(src);
     return rc;
 }
+
+/* ------------------------------------------------------------------------------ */
+/* Closeness (Table 1: "closeness", shortest-path search from each node, and its    */
+/* approximation after Eppstein and Wang with s sampled sources).  For every vertex */
+/* v:  far[v] = scale * sum of d(s, v) over the sources s != v that reach v,        */
+/*     reach[v] = scale * number of those sources.                                 */
+/* Exact: all n sources, scale 1, closeness(v) = reach[v] / far[v] (which is        */
+/* (n-1) / sum_u d(u, v) on a connected graph).  Sampled: k uniform sources, scale  */
+/* n/k, the Eppstein-Wang estimate of the distance sum.                            */
+/* ------------------------------------------------------------------------------ */
+
+int or_closeness(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t k,
+                 const int32_t *src, double scale, double *far, double *reach)
+{
+    if (n < 1 || k < 0) return OR_ERR_ARG;
+    for (int32_t i = 0; i < k; ++i)
+        if (src[i] < 0 || src[i] >= n) return OR_ERR_ARG;
+    int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    if (!dist || !queue) { free(dist); free(queue); return OR_ERR_NOMEM; }
+    for (int32_t v = 0; v < n; ++v) { far[v] = 0.0; reach[v] = 0.0; }
+    for (int32_t i = 0; i < k; ++i) {
+        int32_t s = src[i];
+        for (int32_t v = 0; v < n; ++v) dist[v] = -1;
+        dist[s] = 0;
+        int32_t head = 0, tail = 0;
+        queue[tail++] = s;
+        while (head < tail) {
+            int32_t v = queue[head++];
+            for (int32_t j = row_ptr[v]; j < row_ptr[v + 1]; ++j) {
+                int32_t w = col[j];
+                if (dist[w] < 0) {
+                    dist[w] = dist[v] + 1;
+                    queue[tail++] = w;
+                    far[w] += (double)dist[w];
+                    reach[w] += 1.0;
+                }
+            }
+        }
+    }
+    for (int32_t v = 0; v < n; ++v) { far[v] *= scale; reach[v] *= scale; }
+    free(dist);
+    free(queue);
+    return OR_OK;
+}

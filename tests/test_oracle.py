@@ -456,3 +456,45 @@ def test_rmat_quadrant_frequencies():
             assert abs(f - E * p) < 5 * math.sqrt(E * p * (1 - p))
     n, rp, col = oracle.generate("rmat", 10, 1)
     check_canonical(n, rp, col)
+
+
+# ------------------------------------------------------------------ closeness (Table 1)
+def test_closeness_closed_forms():
+    n = 9
+    _, rp, col = csr(G.path(n))
+    far, reach = oracle.closeness_exact(rp, col)
+    i = np.arange(n)
+    assert np.array_equal(far, (i * (i + 1) / 2 + (n - 1 - i) * (n - i) / 2).astype(float))
+    assert np.all(reach == n - 1)
+    _, rp, col = csr(G.star(7))
+    far, reach = oracle.closeness_exact(rp, col)
+    assert far[0] == 6 and np.all(far[1:] == 1 + 2 * 5)
+    _, rp, col = csr(G.complete(6))
+    far, reach = oracle.closeness_exact(rp, col)
+    assert np.all(far == 5) and np.all(reach == 5)
+    r = 6
+    _, rp, col = csr(G.cycle(2 * r + 1))
+    far, _ = oracle.closeness_exact(rp, col)
+    assert np.all(far == r * (r + 1))
+
+
+@pytest.mark.parametrize("graph", [G.gnp(40, 0.08, 3), G.grid(5, 7), G.random_tree(50, 2),
+                                   G.disjoint_union(G.path(6), G.gnp(20, 0.2, 4), G.complete(1))])
+def test_closeness_matches_floyd_warshall(graph):
+    n, rp, col = csr(graph)
+    d = floyd_warshall(*graph)
+    far, reach = oracle.closeness_exact(rp, col)
+    dd = np.where(d > 0, d, 0)
+    assert np.array_equal(far, dd.sum(0).astype(float))
+    assert np.array_equal(reach, (d > 0).sum(0).astype(float))
+
+
+def test_closeness_sampled_unbiased_and_k_equals_n():
+    n, rp, col = oracle.generate("er", 150, 7, avg_deg=5.0)
+    far, reach = oracle.closeness_exact(rp, col)
+    fs, rs = oracle.closeness_sampled(rp, col, 3, n)
+    assert np.array_equal(fs, far) and np.array_equal(rs, reach)
+    runs = np.stack([oracle.closeness_sampled(rp, col, s, 15)[0] for s in range(300)])
+    mean, se = runs.mean(0), runs.std(0, ddof=1) / np.sqrt(len(runs))
+    z = np.abs(mean - far) / np.maximum(se, 1e-12)
+    assert np.mean(z < 4) > 0.99
