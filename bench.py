@@ -434,6 +434,33 @@ def run_ours(args, world, rank, local):
         out["cuda_graph"] = {"value": world * m * k * args.steps / (gtot / 1e3) / 1e9, "unit": UNIT,
                              "ms_per_step": gtot / args.steps}
 
+    # ---- closeness from the same sources: the forward sweep alone (Table 1, closeness
+    #      and its sampled estimate), device outputs
+    if not exact and rank == 0:
+        far_d = torch.empty(n, dtype=torch.float64, device="cuda")
+        reach_d = torch.empty(n, dtype=torch.float64, device="cuda")
+        co = nk.RunOpts.from_buffer_copy(opts)
+        co.flags &= ~nk.RUN_CUDA_GRAPH
+        for _ in range(max(args.warmup, 1)):
+            nk.closeness_sampled(g, sseed, k, co, out=(far_d, reach_d))
+        torch.cuda.synchronize()
+        cms, ckern, claunch = [], 0.0, 0
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0.record(stream)
+            nk.closeness_sampled(g, sseed, k, co, out=(far_d, reach_d))
+            ev1.record(stream)
+            ev1.synchronize()
+            cms.append(ev0.elapsed_time(ev1))
+            cs = nk.last_run_stats()
+            ckern += cs["kernel_ms"]
+            claunch += cs["launches"]
+        ctot = sum(cms)
+        out["closeness"] = {"value": m * k * args.steps / (ctot / 1e3) / 1e9, "unit": UNIT,
+                            "ms_per_step": ctot / args.steps,
+                            "avg_launch_ms": ckern / max(claunch, 1), "batch": B,
+                            "form": "batched forward sweep, sampled sources, scale n/k"}
+
     # ---- plain per-source form on the same workload (the baseline it beats)
     if not args.no_per_source and rank == 0:
         po = nk.run_opts(mode=nk.MODE_PER_SOURCE, flags=nk.RUN_TIME_KERNELS)

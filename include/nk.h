@@ -194,6 +194,20 @@ int nk_last_run_stats(nk_run_stats *out);
  * calls with batch/alpha = 0 use it). */
 int nk_autotune(const nk_graph *g, uint64_t seed, int32_t k, nk_run_opts *best);
 
+/* ---------------------------------------------------------------- closeness (Table 1) */
+/* Closeness from the same forward sweep (Table 1: closeness by a shortest-path search from
+ * each node, and the approximation after Eppstein and Wang from s sampled sources).  For
+ * every vertex v, with S the source set:
+ *     far[v]   = scale * sum of d(s, v) over the sources s in S, s != v, that reach v,
+ *     reach[v] = scale * number of those sources,
+ * so that closeness(v) = reach[v] / far[v] ((n-1) / sum_u d(u, v) on a connected graph).
+ * Exact: S = V, scale 1 (the sums are exact integers).  Sampled: S from
+ * nk_sample_sources(n, seed, k), scale n/k.  far and reach hold n doubles each (device
+ * pointers with NK_RUN_DEVICE_PTRS).  The batched form runs its forward sweep only. */
+int nk_closeness_exact(const nk_graph *g, double *far, double *reach);
+int nk_closeness_sampled(const nk_graph *g, uint64_t seed, int32_t k, double *far, double *reach,
+                         const nk_run_opts *opts);
+
 /* ---------------------------------------------------------------- serving runtime */
 typedef struct nk_server nk_server;
 typedef int64_t nk_req;

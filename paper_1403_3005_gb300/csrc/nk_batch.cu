@@ -91,6 +91,9 @@ struct BArgs {
     int32_t H, C;
     unsigned long long *part;    // [C][B] per-chunk partial sums (uint64 or double)
     unsigned long long *trace;   // [kTraceCap][2] (code, globaltimer) after each barrier, or null
+    unsigned long long *far;     // [n] closeness: sums of distances from the batch's sources, or null
+    unsigned long long *reach;   // [n] closeness: number of the batch's sources that reach v
+    int backward;                // 0: forward sweep only (closeness)
 };
 
 template <int W> struct Bits {
@@ -691,6 +694,31 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
         a.ctrl->bu_levels = bu;
     }
     if (ovf) atomicOr(&a.ctrl->ovf, 1);
+    if (a.far) {
+        // closeness: v is at distance l from the sources of F_l[v]; one thread per vertex
+        // adds its level sums once the whole sweep has stayed within the slabs (a batch
+        // that ran out of levels returned above and adds nothing).  A bottom-up level takes
+        // its new bits from non-zero path sums, which a sum that wrapped past 2^64 could
+        // hide: a batch with an overflow adds nothing either and the host reruns it.
+        if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+        if (dev::ld_volatile(&a.ctrl->ovf) != 0) return;
+        for (long long v = tid; v < a.n; v += nthr) {
+            unsigned long long fs = 0, rs = 0;
+            for (int l = 1; l <= D; ++l) {
+                const Bits<W> f = load_bits<W>(a.F + (size_t)l * slab + (size_t)v * W);
+                unsigned long long cnt = 0;
+#pragma unroll
+                for (int q = 0; q < W; ++q) cnt += (unsigned long long)__popcll(f.w[q]);
+                fs += cnt * (unsigned long long)l;
+                rs += cnt;
+            }
+            if (rs) {
+                a.far[v] += fs;
+                a.reach[v] += rs;
+            }
+        }
+    }
+    if (!a.backward) return;
 
     // ---- backward sweep, deepest level first
     for (int l = D; l >= 1; --l) {
@@ -892,6 +920,9 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
         a.C = g->heavy_C;
         a.part = reinterpret_cast<unsigned long long *>(base + L.off_part);
         a.trace = nullptr;
+        a.far = cfg.far;
+        a.reach = cfg.reach;
+        a.backward = cfg.backward ? 1 : 0;
         a.limit_ns = cfg.limit_ns ? cfg.limit_ns : wait_limit_ns();
         a.alpha = alpha_used;
         a.dir = cfg.direction;
@@ -955,9 +986,12 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
             ovf |= h[bi].ovf != 0;
             if (h[bi].err == kErrDepth) deep.push_back(bi);
         }
-        if (ovf) return set_error(NK_ERR_OVERFLOW, "a shortest-path count exceeded 2^64 - 1");
+        if (ovf && !cfg.far) return set_error(NK_ERR_OVERFLOW, "a shortest-path count exceeded 2^64 - 1");
+        if (cfg.far)  // closeness: batches with a wrapped path count go to the per-source form
+            for (int bi : todo)
+                if (h[bi].ovf && h[bi].err != kErrDepth) deep.push_back(bi);
         if (deep.empty()) return NK_OK;
-        if (lcap < lmax) {
+        if (lcap < lmax && !(cfg.far && ovf)) {
             todo = deep;
             lcap = lmax;
             continue;
@@ -1029,6 +1063,9 @@ int enqueue_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scor
     a.C = g->heavy_C;
     a.part = reinterpret_cast<unsigned long long *>(base + L.off_part);
     a.trace = nullptr;
+    a.far = cfg.far;
+    a.reach = cfg.reach;
+    a.backward = cfg.backward ? 1 : 0;
     a.limit_ns = cfg.limit_ns ? cfg.limit_ns : wait_limit_ns();
     a.alpha = cfg.alpha > 0 ? cfg.alpha : 1.0;
     a.dir = cfg.direction;

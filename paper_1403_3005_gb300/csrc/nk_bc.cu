@@ -240,6 +240,78 @@ int bc_entry(const nk_graph *gc, const int32_t *src, int32_t k, bool sample, uin
     return NK_OK;
 }
 
+__global__ void k_finish_closeness(const unsigned long long *far_u, const unsigned long long *reach_u,
+                                   int32_t n, double scale, double *far, double *reach)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        far[v] = (double)far_u[v] * scale;
+        reach[v] = (double)reach_u[v] * scale;
+    }
+}
+
+// Closeness entry: all vertices (exact, scale 1) or k sampled sources (scale n/k).
+int closeness_entry(const nk_graph *gc, bool sample, uint64_t seed, int32_t k, double *far,
+                    double *reach, const nk_run_opts *opts)
+{
+    if (!gc) return set_error(NK_ERR_ARG, "graph is null");
+    if (!far || !reach) return set_error(NK_ERR_ARG, "far or reach is null");
+    nk_graph *g = const_cast<nk_graph *>(gc);
+    const int32_t n = g->n;
+    if (sample && (k < 1 || k > n)) return set_error(NK_ERR_ARG, "need 1 <= k <= n (k=%d, n=%d)", k, n);
+    if (!sample) k = n;
+    RunCfg cfg = cfg_of(opts, g);
+    NK_TRY(check_cfg(cfg));
+    const bool dev = opts && (opts->flags & NK_RUN_DEVICE_PTRS);
+    cudaStream_t s = stream();
+    std::lock_guard<std::mutex> lock(g->mu);
+    Tmp dsrc, sums, hfar, hreach;
+    NK_TRY(dsrc.alloc(sizeof(int32_t) * k, s));
+    if (sample) {
+        NK_TRY(sample_sources_device(n, seed, k, dsrc.as<int32_t>(), s));
+    } else {
+        k_iota<<<std::max(1, std::min((k + 255) / 256, 8 * num_sms())), 256, 0, s>>>(dsrc.as<int32_t>(), k);
+        ::nk::count_launch();
+    }
+    NK_TRY(sums.alloc(sizeof(unsigned long long) * 2 * (size_t)n, s));
+    unsigned long long *far_u = sums.as<unsigned long long>(), *reach_u = far_u + n;
+    NK_CUDA(cudaMemsetAsync(sums.p, 0, sizeof(unsigned long long) * 2 * (size_t)n, s));
+    cfg.far = far_u;
+    cfg.reach = reach_u;
+    cfg.backward = false;
+    t_stats = RunStats();
+    int mode = cfg.mode == NK_MODE_AUTO ? (k >= 16 ? NK_MODE_BATCHED : NK_MODE_PER_SOURCE) : cfg.mode;
+    int rc;
+    if (mode == NK_MODE_BATCHED) {
+        rc = run_batched(g, dsrc.as<int32_t>(), k, nullptr, cfg, &t_stats, s);
+        if (rc == NK_ERR_NOMEM && cfg.mode == NK_MODE_AUTO) {
+            NK_CUDA(cudaMemsetAsync(sums.p, 0, sizeof(unsigned long long) * 2 * (size_t)n, s));
+            t_stats = RunStats();
+            rc = run_per_source(g, dsrc.as<int32_t>(), k, nullptr, cfg, &t_stats, s);
+        }
+    } else {
+        rc = run_per_source(g, dsrc.as<int32_t>(), k, nullptr, cfg, &t_stats, s);
+    }
+    NK_TRY(rc);
+    double *dfar = far, *dreach = reach;
+    if (!dev) {
+        NK_TRY(hfar.alloc(sizeof(double) * n, s));
+        NK_TRY(hreach.alloc(sizeof(double) * n, s));
+        dfar = hfar.as<double>();
+        dreach = hreach.as<double>();
+    }
+    const double scale = sample ? (double)n / (double)k : 1.0;
+    k_finish_closeness<<<std::max(1, std::min((n + 255) / 256, 8 * num_sms())), 256, 0, s>>>(far_u, reach_u, n, scale, dfar, dreach);
+    ::nk::count_launch();
+    NK_CUDA(cudaGetLastError());
+    if (!dev) {
+        NK_CUDA(cudaMemcpyAsync(far, dfar, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        NK_CUDA(cudaMemcpyAsync(reach, dreach, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    }
+    NK_CUDA(cudaStreamSynchronize(s));
+    return NK_OK;
+}
+
 }  // namespace
 }  // namespace nk
 
@@ -271,6 +343,17 @@ int nk_betweenness_sources(const nk_graph *g, const int32_t *src, int32_t k, dou
 {
     if (!src) return set_error(NK_ERR_ARG, "src is null");
     return bc_entry(g, src, k, false, 0, scale, scores, opts);
+}
+
+int nk_closeness_exact(const nk_graph *g, double *far, double *reach)
+{
+    return closeness_entry(g, false, 0, 0, far, reach, nullptr);
+}
+
+int nk_closeness_sampled(const nk_graph *g, uint64_t seed, int32_t k, double *far, double *reach,
+                         const nk_run_opts *opts)
+{
+    return closeness_entry(g, true, seed, k, far, reach, opts);
 }
 
 int nk_last_run_stats(nk_run_stats *out)

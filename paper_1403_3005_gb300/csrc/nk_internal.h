@@ -176,6 +176,9 @@ struct RunCfg {
     int grid_ctas = 0;     // if > 0: persistent grids use at most this many CTAs
     int lcap = 0;          // batched level slabs; 0 = sized from free memory
     uint64_t limit_ns = 0; // bound on device-side waits; 0 = the process-wide bound
+    bool backward = true;  // false: forward sweep only
+    unsigned long long *far = nullptr;    // closeness distance sums (device), or null
+    unsigned long long *reach = nullptr;  // closeness reach counts (device), or null
 };
 
 inline DevBuf *scratch(const RunCfg &c, nk_graph *g);

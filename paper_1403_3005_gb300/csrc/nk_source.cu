@@ -374,6 +374,21 @@ __global__ void __launch_bounds__(kThreads) k_source(SrcArgs a)
     }
 }
 
+// closeness from a forward sweep: every reached vertex other than the source adds its
+// distance and one to its sums
+__global__ void k_add_distances(const int32_t *dist, int32_t n, unsigned long long *far,
+                                unsigned long long *reach)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int d = dist[v];
+        if (d > 0) {
+            far[v] += (unsigned long long)d;
+            reach[v] += 1ull;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ host side
 struct Launch {
     const void *fn;
@@ -471,6 +486,7 @@ int run(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores, const Ru
         NK_CUDA(cudaEventCreate(&e1));
         NK_CUDA(cudaEventRecord(e0, s));
     }
+    if (cfg.far) a.forward_only = 1;
     for (int32_t i = 0; i < k; ++i) {
         a.src = d_src + i;
         void *args[] = {&a};
@@ -478,6 +494,10 @@ int run(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores, const Ru
         if (cfg.grid_ctas > 0) grid = std::min(grid, cfg.grid_ctas);
         NK_CUDA(cudaLaunchCooperativeKernel(L.fn, dim3(grid), dim3(kThreads), args, 0, s));
         ::nk::count_launch();
+        if (cfg.far) {
+            k_add_distances<<<std::max(1, std::min((n + 255) / 256, 8 * num_sms())), 256, 0, s>>>(a.dist, n, cfg.far, cfg.reach);
+            ::nk::count_launch();
+        }
     }
     if (cfg.time_kernels) NK_CUDA(cudaEventRecord(e1, s));
     Ctrl h;
@@ -501,7 +521,8 @@ int run(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores, const Ru
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (h.err) return set_error(h.err, "per-source sweep aborted: a bounded grid wait ran out");
-    if (h.ovf) return set_error(NK_ERR_OVERFLOW, "a shortest-path count exceeded 2^64 - 1");
+    // closeness needs distances only, which do not depend on the path counts
+    if (h.ovf && !cfg.far) return set_error(NK_ERR_OVERFLOW, "a shortest-path count exceeded 2^64 - 1");
     return NK_OK;
 }
 

@@ -93,6 +93,8 @@ SIGNATURES = {
     "nk_betweenness_sampled": (_INT, [_P, _U64, _I32, _P]),
     "nk_betweenness_sampled_opts": (_INT, [_P, _U64, _I32, _P, _P]),
     "nk_betweenness_sources": (_INT, [_P, _P, _I32, _D, _P, _P]),
+    "nk_closeness_exact": (_INT, [_P, _P, _P]),
+    "nk_closeness_sampled": (_INT, [_P, _U64, _I32, _P, _P, _P]),
     "nk_last_run_stats": (_INT, [_P]),
     "nk_autotune": (_INT, [_P, _U64, _I32, _P]),
     "nk_server_create": (_INT, [_P, _P]),
@@ -322,6 +324,37 @@ def betweenness_sources(g: Graph, src, scale: float, opts: RunOpts | None = None
     _check(lib().nk_betweenness_sources(g.handle, sp, k, scale, ptr,
                                          ctypes.byref(o) if o is not None else None))
     return res
+
+
+def closeness_exact(g: Graph):
+    """(far, reach) over all sources: sum of distances and count of sources reaching
+    each vertex; closeness = reach / far."""
+    far = np.empty(g.n, np.float64)
+    reach = np.empty(g.n, np.float64)
+    _check(lib().nk_closeness_exact(g.handle, _np_ptr(far), _np_ptr(reach)))
+    return far, reach
+
+
+def closeness_sampled(g: Graph, seed: int, k: int, opts: RunOpts | None = None, out=None):
+    """(far, reach) from k sampled sources, scaled by n/k (Eppstein-Wang estimate).
+    out: None (new host arrays) or a pair of float64 CUDA tensors of n entries."""
+    if out is not None:
+        far, reach = out
+        if not (_is_torch(far) and _is_torch(reach)):
+            raise ValueError("out must be a pair of CUDA tensors")
+        o = run_opts() if opts is None else RunOpts.from_buffer_copy(opts)
+        o.flags |= RUN_DEVICE_PTRS
+        _check(lib().nk_closeness_sampled(g.handle, seed, k, _dev_ptr(far), _dev_ptr(reach),
+                                          ctypes.byref(o)))
+        return far, reach
+    far = np.empty(g.n, np.float64)
+    reach = np.empty(g.n, np.float64)
+    if opts is not None and (opts.flags & RUN_DEVICE_PTRS):
+        opts = RunOpts.from_buffer_copy(opts)
+        opts.flags &= ~RUN_DEVICE_PTRS
+    _check(lib().nk_closeness_sampled(g.handle, seed, k, _np_ptr(far), _np_ptr(reach),
+                                      ctypes.byref(opts) if opts is not None else None))
+    return far, reach
 
 
 def last_run_stats() -> dict:

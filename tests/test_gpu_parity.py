@@ -297,3 +297,50 @@ def test_cuda_graph_capture_and_replay(nk):
     outp = torch.empty(400, dtype=torch.float64, device="cuda")
     nk.betweenness_sampled(gp, 2, 100, nk.run_opts(mode=2, batch=64, flags=flags), out=outp)
     assert close(outp.cpu().numpy(), oracle.betweenness_sampled(rpp, colp, 2, 100))
+
+
+# ------------------------------------------------------------------ closeness (Table 1)
+@pytest.mark.parametrize("name", ["path", "star", "cycle_odd", "grid", "components", "hubs", "tree"])
+def test_closeness_exact_small(nk, name):
+    g, rp, col = both(nk, SMALL[name])
+    far0, reach0 = oracle.closeness_exact(rp, col)
+    far, reach = nk.closeness_exact(g)
+    assert np.array_equal(far, far0) and np.array_equal(reach, reach0)
+    n = len(rp) - 1
+    for m in (dict(mode=1), dict(mode=2, batch=64, direction=1), dict(mode=2, batch=256, direction=2)):
+        f2, r2 = nk.closeness_sampled(g, 5, n, nk.run_opts(**m))
+        assert np.array_equal(f2, far0) and np.array_equal(r2, reach0), m
+
+
+def test_closeness_sampled_generated(nk):
+    for kind, size, params, k in (("rmat", 14, {}, 500), ("ba", 50000, dict(m0=4), 300)):
+        g = nk.graph_generate(kind, size, 3, **params)
+        n, rp, col = oracle.generate(kind, size, 3, **params)
+        f0, r0 = oracle.closeness_sampled(rp, col, 9, k)
+        f1, r1 = nk.closeness_sampled(g, 9, k)
+        assert np.array_equal(f1, f0) and np.array_equal(r1, r0), kind
+    gp, rpp, colp = both(nk, G.path(3000))   # deeper than the level slabs: per-source fallback
+    f0, r0 = oracle.closeness_sampled(rpp, colp, 4, 70)
+    f1, r1 = nk.closeness_sampled(gp, 4, 70, nk.run_opts(mode=2, batch=64))
+    assert np.array_equal(f1, f0) and np.array_equal(r1, r0)
+
+
+def test_closeness_with_path_count_overflow(nk):
+    # 35 x 35 grid: corner-to-corner path counts exceed 2^64 - 1; distances are unaffected,
+    # so closeness succeeds in every form (batched sweeps rerun such batches per source)
+    g, rp, col = both(nk, G.grid(35, 35))
+    far0, reach0 = oracle.closeness_exact(rp, col)
+    for m in (dict(mode=1), dict(mode=2, batch=64), dict(mode=2, batch=128, direction=2)):
+        f, r = nk.closeness_sampled(g, 1, len(rp) - 1, nk.run_opts(**m))
+        assert np.array_equal(f, far0) and np.array_equal(r, reach0), m
+
+
+def test_closeness_device_outputs(nk):
+    import torch
+    g = nk.graph_generate("rmat", 13, 2)
+    n, rp, col = oracle.generate("rmat", 13, 2)
+    f0, r0 = oracle.closeness_sampled(rp, col, 6, 200)
+    far = torch.full((n,), -1.0, dtype=torch.float64, device="cuda")
+    reach = torch.full((n,), -1.0, dtype=torch.float64, device="cuda")
+    nk.closeness_sampled(g, 6, 200, nk.run_opts(mode=2, batch=128), out=(far, reach))
+    assert np.array_equal(far.cpu().numpy(), f0) and np.array_equal(reach.cpu().numpy(), r0)
