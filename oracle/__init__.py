@@ -6,8 +6,8 @@ this package, and this package never imports the product library.
 
 Every function mirrors one C function and cites the passage of the paper it follows:
 Brandes' algorithm and the sampled estimate (Section 3.2, Table 1), BFS for unweighted
-graphs (Section 3.4), closeness exact and sampled (Table 1), the generators of Section 5
-(Table 2).
+graphs (Section 3.4), edge betweenness (Section 4.3), closeness exact and sampled (Table 1),
+the generators of Section 5 (Table 2).
 """
 from __future__ import annotations
 
@@ -68,6 +68,7 @@ def _load():
             "or_betweenness_exact": (ctypes.c_int, [i32, P, P, P]),
             "or_betweenness_sampled": (ctypes.c_int, [i32, P, P, u64, i32, P]),
             "or_closeness": (ctypes.c_int, [i32, P, P, i32, P, dbl, P, P]),
+            "or_edge_betweenness": (ctypes.c_int, [i32, P, P, i32, P, dbl, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -216,6 +217,29 @@ def betweenness_sampled(rp, col, seed: int, k: int) -> np.ndarray:
     if rc:
         raise OracleError(rc, "betweenness_sampled")
     return out
+
+
+# ---------------------------------------------------------------- edge betweenness (Section 4.3)
+def edge_betweenness_sources(rp, col, src, scale: float) -> np.ndarray:
+    """Per arc j of the CSR: scale * (sum over the arc + sum over its reverse arc) of the
+    shares sigma_v / sigma_w * (1 + delta_w); both arcs of an edge hold the edge's score."""
+    rp, col, src = _i32(rp), _i32(col), _i32(src)
+    n = len(rp) - 1
+    out = np.empty(max(len(col), 1), np.float64)
+    rc = _load().or_edge_betweenness(n, _p(rp), _p(col), len(src), _p(src), scale, _p(out))
+    if rc:
+        raise OracleError(rc, "edge_betweenness")
+    return out[:len(col)]
+
+
+def edge_betweenness_exact(rp, col) -> np.ndarray:
+    n = len(rp) - 1
+    return edge_betweenness_sources(rp, col, np.arange(n, dtype=np.int32), 0.5)
+
+
+def edge_betweenness_sampled(rp, col, seed: int, k: int) -> np.ndarray:
+    n = len(rp) - 1
+    return edge_betweenness_sources(rp, col, sample_sources(n, seed, k), n / (2.0 * k))
 
 
 # ---------------------------------------------------------------- closeness (Table 1)

@@ -446,6 +446,86 @@ int or_betweenness_sampled(int32_t n, const int32_t *row_ptr, const int32_t *col
 }
 
 /* ------------------------------------------------------------------------------ */
+/* Edge betweenness (Section 4.3: edge centrality by the shortest paths through an  */
+/* edge).  Brandes' sweep again; every term sigma[v] / sigma[w] * (1 + delta[w])    */
+/* that flows from w to its predecessor v is the share of the pairs (s, t) whose    */
+/* shortest paths use the edge {v, w}, so it is added to that edge as well as to    */
+/* delta[v].  Per arc j of the CSR (u -> x), out[j] = scale * (sum over the arc u->x */
+/* + sum over the reverse arc x->u): both arcs of an edge hold the edge's score.    */
+/* Exact: all sources, scale 1/2 (unordered pairs); sampled: scale n/(2k).           */
+/* ------------------------------------------------------------------------------ */
+
+/* index of the arc v -> u in the sorted row of v, or -1 */
+static int64_t or_find_arc(const int32_t *row_ptr, const int32_t *col, int32_t v, int32_t u)
+{
+    int64_t lo = row_ptr[v], hi = row_ptr[v + 1];
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (col[mid] < u) lo = mid + 1; else hi = mid;
+    }
+    return (lo < row_ptr[v + 1] && col[lo] == u) ? lo : -1;
+}
+
+int or_edge_betweenness(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t k,
+                        const int32_t *src, double scale, double *out)
+{
+    if (n < 1 || k < 0) return OR_ERR_ARG;
+    for (int32_t i = 0; i < k; ++i)
+        if (src[i] < 0 || src[i] >= n) return OR_ERR_ARG;
+    const int64_t A = row_ptr[n];
+    double *delta = (double *)malloc(sizeof(double) * (size_t)n);
+    double *arc = (double *)calloc((size_t)(A > 0 ? A : 1), sizeof(double));
+    or_ws ws;
+    int rc = (delta && arc) ? or_ws_init(&ws, n, A) : OR_ERR_NOMEM;
+    for (int32_t i = 0; rc == OR_OK && i < k; ++i) {
+        int32_t s = src[i];
+        int32_t *dist = ws.dist, *S = ws.S;
+        uint64_t *sigma = ws.sigma;
+        for (int32_t v = 0; v < n; ++v) { dist[v] = -1; sigma[v] = 0; delta[v] = 0.0; }
+        dist[s] = 0;
+        sigma[s] = 1;
+        int32_t head = 0, tail = 0;
+        S[tail++] = s;
+        while (head < tail) {
+            int32_t v = S[head++];
+            for (int32_t j = row_ptr[v]; j < row_ptr[v + 1]; ++j) {
+                int32_t w = col[j];
+                if (dist[w] < 0) {
+                    dist[w] = dist[v] + 1;
+                    S[tail++] = w;
+                }
+                if (dist[w] == dist[v] + 1 &&
+                    __builtin_add_overflow(sigma[w], sigma[v], &sigma[w])) rc = OR_ERR_OVERFLOW;
+            }
+        }
+        if (rc != OR_OK) break;
+        /* deepest first: w hands its share to every predecessor v over the arc w -> v */
+        while (tail > 0) {
+            int32_t w = S[--tail];
+            for (int32_t j = row_ptr[w]; j < row_ptr[w + 1]; ++j) {
+                int32_t v = col[j];
+                if (dist[v] != dist[w] - 1) continue;
+                double c = ((double)sigma[v] / (double)sigma[w]) * (1.0 + delta[w]);
+                delta[v] += c;
+                arc[j] += c;
+            }
+        }
+    }
+    if (rc == OR_OK) {
+        for (int32_t u = 0; u < n; ++u)
+            for (int32_t j = row_ptr[u]; j < row_ptr[u + 1]; ++j) {
+                int64_t r = or_find_arc(row_ptr, col, col[j], u);
+                if (r < 0) { rc = OR_ERR_GRAPH; break; }
+                out[j] = scale * (arc[j] + arc[r]);
+            }
+    }
+    if (delta && arc) or_ws_free(&ws);
+    free(delta);
+    free(arc);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------------ */
 /* Closeness (Table 1: "closeness", shortest-path search from each node, and its    */
 /* approximation after Eppstein and Wang with s sampled sources).  For every vertex */
 /* v:  far[v] = scale * sum of d(s, v) over the sources s != v that reach v,        */

@@ -102,3 +102,22 @@ def betweenness_bruteforce(n, u, v):
             if cnt[x]:
                 c[x] += Fraction(cnt[x], len(ps))
     return c
+
+
+def edge_betweenness_bruteforce(n, u, v):
+    """{(a, b), a < b: exact rational edge betweenness}: over unordered reachable pairs
+    {s, t}, the fraction of shortest s-t paths that use the edge."""
+    adj = adjacency(n, u, v)
+    c = {}
+    for a in range(n):
+        for b in adj[a]:
+            if a < b:
+                c[(a, b)] = Fraction(0)
+    for s, t in itertools.combinations(range(n), 2):
+        ps = enumerate_shortest_paths(adj, s, t)
+        if not ps:
+            continue
+        for p in ps:
+            for x, y in zip(p[:-1], p[1:]):
+                c[(min(x, y), max(x, y))] += Fraction(1, len(ps))
+    return c

@@ -498,3 +498,109 @@ def test_closeness_sampled_unbiased_and_k_equals_n():
     mean, se = runs.mean(0), runs.std(0, ddof=1) / np.sqrt(len(runs))
     z = np.abs(mean - far) / np.maximum(se, 1e-12)
     assert np.mean(z < 4) > 0.99
+
+
+# ------------------------------------------------------------------ edge betweenness (Section 4.3)
+def edge_values(n, rp, col, e):
+    """{(a, b), a < b: value} from per-arc scores; both arcs of an edge must agree."""
+    out = {}
+    for a in range(n):
+        for j in range(rp[a], rp[a + 1]):
+            b = int(col[j])
+            key = (min(a, b), max(a, b))
+            if key in out:
+                assert out[key] == e[j], key
+            out[key] = e[j]
+    return out
+
+
+def test_edge_betweenness_closed_forms():
+    n = 10
+    _, rp, col = csr(G.path(n))
+    ev = edge_values(n, rp, col, oracle.edge_betweenness_exact(rp, col))
+    assert all(ev[(i, i + 1)] == (i + 1) * (n - 1 - i) for i in range(n - 1))
+    _, rp, col = csr(G.star(8))
+    assert np.all(oracle.edge_betweenness_exact(rp, col) == 7)
+    _, rp, col = csr(G.complete(7))
+    assert np.all(oracle.edge_betweenness_exact(rp, col) == 1)
+    r = 5
+    _, rp, col = csr(G.cycle(2 * r + 1))
+    assert np.allclose(oracle.edge_betweenness_exact(rp, col), r * (r + 1) / 2, rtol=1e-14)
+    _, rp, col = csr(G.cycle(2 * r))
+    assert np.allclose(oracle.edge_betweenness_exact(rp, col), r * r / 2, rtol=1e-14)
+    a, b = 4, 7
+    _, rp, col = csr(G.complete_bipartite(a, b))
+    assert np.allclose(oracle.edge_betweenness_exact(rp, col), 1 + (a - 1) / b + (b - 1) / a, rtol=1e-14)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_edge_betweenness_tree_side_products(seed):
+    n = 200
+    g = G.random_tree(n, seed)
+    _, rp, col = csr(g)
+    ev = edge_values(n, rp, col, oracle.edge_betweenness_exact(rp, col))
+    adj = [[] for _ in range(n)]
+    for x, y in zip(g[1].tolist(), g[2].tolist()):
+        adj[x].append(y)
+        adj[y].append(x)
+    for (x, y), val in list(ev.items())[::5]:
+        seen, stack = {x, y}, [y]          # the side of y once {x, y} is cut
+        while stack:
+            z = stack.pop()
+            for w in adj[z]:
+                if w not in seen:
+                    seen.add(w)
+                    stack.append(w)
+        side = len(seen) - 1
+        assert val == side * (n - side)
+
+
+def _edge_close(n, rp, col, e, ref):
+    ev = edge_values(n, rp, col, e)
+    assert set(ev) == set(ref)
+    return all(math.isclose(ev[key], float(ref[key]), rel_tol=1e-12, abs_tol=1e-12) for key in ref)
+
+
+def test_edge_betweenness_all_graphs_on_5_vertices():
+    from bruteforce import edge_betweenness_bruteforce
+    for mask in range(0, 1 << 10, 3):
+        g = G.from_mask(5, mask)
+        n, rp, col = csr(g)
+        assert _edge_close(n, rp, col, oracle.edge_betweenness_exact(rp, col), edge_betweenness_bruteforce(*g)), mask
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_edge_betweenness_random_small_bruteforce(seed):
+    from bruteforce import edge_betweenness_bruteforce
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(6, 12))
+    g = (G.gnp(n, float(rng.uniform(0.2, 0.6)), seed) if seed % 3 else
+         G.disjoint_union(G.gnp(n // 2, 0.6, seed), G.random_tree(n - n // 2, seed)))
+    n, rp, col = csr(g)
+    assert _edge_close(n, rp, col, oracle.edge_betweenness_exact(rp, col), edge_betweenness_bruteforce(*g))
+
+
+@pytest.mark.parametrize("graph", [G.gnp(120, 0.05, 4), G.grid(9, 13),
+                                   G.disjoint_union(G.cycle(30), G.gnp(60, 0.1, 5), G.star(9))])
+def test_edge_betweenness_invariants(graph):
+    # sum over edges = sum over reachable unordered pairs of d(s, t); and at every vertex the
+    # incident edges carry 2 c_B(v) + reach(v) (an interior vertex of a path meets two of
+    # its edges, an endpoint one)
+    n, rp, col = csr(graph)
+    e = oracle.edge_betweenness_exact(rp, col)
+    d = floyd_warshall(*graph)
+    assert math.isclose(e.sum() / 2, d[d > 0].sum() / 2, rel_tol=1e-12)
+    cb = oracle.betweenness_exact(rp, col)
+    _, reach = oracle.closeness_exact(rp, col)
+    inc = np.array([e[rp[v]:rp[v + 1]].sum() for v in range(n)])
+    assert np.allclose(inc, 2 * cb + reach, rtol=1e-12, atol=1e-12)
+
+
+def test_edge_betweenness_sampled_unbiased_and_k_equals_n():
+    n, rp, col = oracle.generate("er", 120, 5, avg_deg=5.0)
+    e = oracle.edge_betweenness_exact(rp, col)
+    assert np.array_equal(oracle.edge_betweenness_sampled(rp, col, 4, n), e)
+    runs = np.stack([oracle.edge_betweenness_sampled(rp, col, s, 12) for s in range(300)])
+    mean, se = runs.mean(0), runs.std(0, ddof=1) / np.sqrt(len(runs))
+    z = np.abs(mean - e) / np.maximum(se, 1e-12)
+    assert np.mean(z < 4) > 0.99
