@@ -461,6 +461,33 @@ def run_ours(args, world, rank, local):
                             "avg_launch_ms": ckern / max(claunch, 1), "batch": B,
                             "form": "batched forward sweep, sampled sources, scale n/k"}
 
+    # ---- edge betweenness from the same sources (Section 4.3): the same two sweeps with a
+    #      per-arc share in the backward gather, device output of A doubles
+    if not exact and rank == 0:
+        edge_d = torch.empty(A, dtype=torch.float64, device="cuda")
+        eo = nk.RunOpts.from_buffer_copy(opts)
+        eo.flags &= ~nk.RUN_CUDA_GRAPH
+        for _ in range(max(args.warmup, 1)):
+            nk.edge_betweenness_sampled(g, sseed, k, eo, out=edge_d)
+        torch.cuda.synchronize()
+        ems, ekern, elaunch = [], 0.0, 0
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0.record(stream)
+            nk.edge_betweenness_sampled(g, sseed, k, eo, out=edge_d)
+            ev1.record(stream)
+            ev1.synchronize()
+            ems.append(ev0.elapsed_time(ev1))
+            es = nk.last_run_stats()
+            ekern += es["kernel_ms"]
+            elaunch += es["launches"]
+        etot = sum(ems)
+        out["edge_betweenness"] = {"value": m * k * args.steps / (etot / 1e3) / 1e9, "unit": UNIT,
+                                   "ms_per_step": etot / args.steps,
+                                   "avg_launch_ms": ekern / max(elaunch, 1), "batch": B,
+                                   "form": "batched sweeps with per-arc shares, sampled sources, scale n/(2k)"}
+        del edge_d
+
     # ---- plain per-source form on the same workload (the baseline it beats)
     if not args.no_per_source and rank == 0:
         po = nk.run_opts(mode=nk.MODE_PER_SOURCE, flags=nk.RUN_TIME_KERNELS)

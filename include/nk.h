@@ -194,6 +194,23 @@ int nk_last_run_stats(nk_run_stats *out);
  * calls with batch/alpha = 0 use it). */
 int nk_autotune(const nk_graph *g, uint64_t seed, int32_t k, nk_run_opts *best);
 
+/* ---------------------------------------------------------------- edge betweenness (Section 4.3) */
+/* Edge betweenness: for an edge {u, v}, the sum over unordered reachable pairs {s, t} of the
+ * fraction of shortest s-t paths that use the edge (Section 4.3: edge centrality from the
+ * shortest paths through an edge).  Computed in the same sweeps as betweenness: in the
+ * dependency accumulation the share sigma_v / sigma_w * (1 + delta_w) that a vertex w hands
+ * to a predecessor v is also added to the edge {v, w}.
+ * edge_scores holds one double per arc of the canonical CSR (A entries, in the order of
+ * nk_graph_export_csr); both arcs of an edge hold the edge's score.  Exact: all sources,
+ * scale 1/2.  Sampled: the sources of nk_sample_sources(n, seed, k), scale n/(2k).
+ * edge_scores is a device pointer with NK_RUN_DEVICE_PTRS in opts, else host memory.
+ * Errors: NK_ERR_ARG (null pointers, k outside [1, n]), NK_ERR_OVERFLOW (a path count above
+ * 2^64 - 1), NK_ERR_GRAPH (an arc without its reverse arc), NK_ERR_NOMEM, NK_ERR_TIMEOUT.
+ * Device memory: 8A + 8n bytes besides the sweep's own workspace. */
+int nk_edge_betweenness_exact(const nk_graph *g, double *edge_scores);
+int nk_edge_betweenness_sampled(const nk_graph *g, uint64_t seed, int32_t k, double *edge_scores,
+                                const nk_run_opts *opts);
+
 /* ---------------------------------------------------------------- closeness (Table 1) */
 /* Closeness from the same forward sweep (Table 1: closeness by a shortest-path search from
  * each node, and the approximation after Eppstein and Wang from s sampled sources).  For

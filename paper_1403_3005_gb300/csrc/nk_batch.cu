@@ -94,6 +94,7 @@ struct BArgs {
     unsigned long long *far;     // [n] closeness: sums of distances from the batch's sources, or null
     unsigned long long *reach;   // [n] closeness: number of the batch's sources that reach v
     int backward;                // 0: forward sweep only (closeness)
+    double *edge;                // [A] edge betweenness: per-arc shares, or null
 };
 
 template <int W> struct Bits {
@@ -176,11 +177,15 @@ __device__ __forceinline__ void check_failed(const BArgs &a, int code, int where
 // carry detection) or double-single sums (psi).  Lanes over neighbours find the relevant
 // ones; then lanes over source bits read the contiguous sp rows, two neighbours per
 // round so that their loads are in flight together.
-template <int W, bool PSI>
+// With EDGE (backward only) the warp's vertex v also hands every relevant arc (v, c) its
+// share sum_b sigma_b(v) * psi_b(c) over the gathered source bits (sv holds sigma_b(v) of
+// the lane's slots): a warp sum per neighbour, added to edge[j] by lane 0.  The arc is
+// owned by v's warp at this level, so no atomics are needed.
+template <int W, bool PSI, bool EDGE = false>
 __device__ __forceinline__ void gather(const BArgs &a, int beg, int end,
                                        const unsigned long long *Fsel, const Bits<W> &tgt,
                                        unsigned long long (&acc)[2 * W], dev::ff (&facc)[2 * W],
-                                       bool &ovf)
+                                       bool &ovf, const dev::ff *sv = nullptr)
 {
     constexpr int B = 64 * W;
     const int lane = threadIdx.x & 31;
@@ -232,6 +237,20 @@ __device__ __forceinline__ void gather(const BArgs &a, int beg, int end,
                 } else {
                     add_carry(acc[k], carry, x0[k]);
                     add_carry(acc[k], carry, x1[k]);
+                }
+            }
+            if constexpr (EDGE) {
+                dev::ff e0 = dev::ff_zero(), e1 = dev::ff_zero();
+#pragma unroll
+                for (int k = 0; k < 2 * W; ++k) {
+                    e0 = dev::ff_add(e0, dev::ff_mul(sv[k], dev::ff_unpack(x0[k])));
+                    e1 = dev::ff_add(e1, dev::ff_mul(sv[k], dev::ff_unpack(x1[k])));
+                }
+                e0 = dev::group_sum_ff<32>(e0);
+                e1 = dev::group_sum_ff<32>(e1);
+                if (lane == 0) {
+                    a.edge[base + s0] += dev::ff_to_double(e0);
+                    if (two) a.edge[base + s1] += dev::ff_to_double(e1);
                 }
             }
         }
@@ -428,7 +447,7 @@ __device__ __forceinline__ void store_part(const BArgs &a, int c, const unsigned
 
 __device__ __forceinline__ bool heavy(const BArgs &a, int v) { return deg_of(a.rp, v) > kChunk; }
 
-template <int W>
+template <int W, bool EDGE>
 __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
 {
     constexpr int B = 64 * W;
@@ -436,7 +455,6 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nthr = (long long)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
-    const long long wid = tid >> 5, nw = nthr >> 5;
     const size_t slab = (size_t)a.n * W;
     Bits<W> act;
 #pragma unroll
@@ -720,8 +738,9 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
     }
     if (!a.backward) return;
 
-    // ---- backward sweep, deepest level first
-    for (int l = D; l >= 1; --l) {
+    // ---- backward sweep, deepest level first (edge betweenness also needs level 0: the
+    //      arcs from the sources carry shares, although the sources get no score)
+    for (int l = D; l >= (EDGE ? 0 : 1); --l) {
         const unsigned long long *Fl = a.F + (size_t)l * slab;
         const unsigned long long *Fs = a.F + (size_t)(l + 1) * slab;
         const int ql = __ldcg(a.qoff + l);
@@ -743,28 +762,38 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
                 }
             }
             part = dev::group_sum_ff<32>(part);
-            if (lane == 0 && part.hi != 0.0f) a.scores[v] += dev::ff_to_double(part);
+            if (lane == 0 && part.hi != 0.0f && l > 0) a.scores[v] += dev::ff_to_double(part);
+        };
+        // sigma_b(v) of the lane's slots in mv (edge betweenness only), read before psi
+        // replaces it
+        auto sigma_row = [&](int v, const Bits<W> &mv, dev::ff (&sv)[2 * W]) {
+            const unsigned long long *row = a.sp + (size_t)v * B + lane;
+#pragma unroll
+            for (int k = 0; k < 2 * W; ++k)
+                sv[k] = has_slot<W>(mv, k, lane) ? dev::ff_from_u64(__ldcg(row + 32 * k)) : dev::ff_zero();
         };
         for_level<W>(a, ql, nl, Fl, a.wq + (size_t)l * 8 + WQ_BACK, [&](int v) {
             if (heavy(a, v)) return;
             const Bits<W> mv = load_bits<W>(Fl + (size_t)v * W);
             unsigned long long acc[2 * W];
-            dev::ff facc[2 * W];
+            dev::ff facc[2 * W], sv[2 * W];
 #pragma unroll
             for (int k = 0; k < 2 * W; ++k) facc[k] = dev::ff_zero();
+            if constexpr (EDGE) sigma_row(v, mv, sv);
             bool dummy = false;
-            gather<W, true>(a, __ldg(a.rp + v), __ldg(a.rp + v + 1), Fs, mv, acc, facc, dummy);
+            gather<W, true, EDGE>(a, __ldg(a.rp + v), __ldg(a.rp + v + 1), Fs, mv, acc, facc, dummy, sv);
             finish(v, mv, facc);
         });
         for_chunks(a, a.wq + (size_t)l * 8 + WQ_BACK_C, [&](int c, int h, int j0, int j1) {
             const Bits<W> mv = load_bits<W>(Fl + (size_t)h * W);
             if (!any_bits<W>(mv)) return;
             unsigned long long acc[2 * W];
-            dev::ff facc[2 * W];
+            dev::ff facc[2 * W], sv[2 * W];
 #pragma unroll
             for (int k = 0; k < 2 * W; ++k) facc[k] = dev::ff_zero();
+            if constexpr (EDGE) sigma_row(h, mv, sv);
             bool dummy = false;
-            gather<W, true>(a, j0, j1, Fs, mv, acc, facc, dummy);
+            gather<W, true, EDGE>(a, j0, j1, Fs, mv, acc, facc, dummy, sv);
 #pragma unroll
             for (int k = 0; k < 2 * W; ++k) acc[k] = dev::ff_pack(facc[k]);
             store_part<W>(a, c, acc);
@@ -790,12 +819,12 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
 }
 
 // ------------------------------------------------------------------ host side
-template <int W> int blocks_per_sm()
+template <int W, bool EDGE = false> int blocks_per_sm()
 {
     static int b = -1;
     if (b < 0) {
         int v = 0;
-        NK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_batch<W>, kThreads, 0));
+        NK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_batch<W, EDGE>, kThreads, 0));
         b = v;
     }
     return b;
@@ -874,8 +903,10 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
     const int lstart = cfg.lcap > 0 ? lmax : std::min(lmax, std::max(kStartLevels, 4));
     const int nb = (k + B - 1) / B;
     NK_TRY(ws[WS_BCTRL].ensure(sizeof(Ctrl) * nb));
-    const int bps = blocks_per_sm<W>();
+    const bool edge = cfg.edge && cfg.backward;
+    const int bps = edge ? blocks_per_sm<W, true>() : blocks_per_sm<W>();
     if (bps < 1) return set_error(NK_ERR_CUDA, "batched kernel cannot be resident");
+    const void *kfn = edge ? (const void *)k_batch<W, true> : (const void *)k_batch<W, false>;
     int grid = std::max(1, bps * num_sms() / std::max(1, cfg.grid_div));
     if (cfg.grid_ctas > 0) grid = std::min(grid, cfg.grid_ctas);
     Ctrl *ctrls = ws[WS_BCTRL].as<Ctrl>();
@@ -923,6 +954,7 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
         a.far = cfg.far;
         a.reach = cfg.reach;
         a.backward = cfg.backward ? 1 : 0;
+        a.edge = edge ? cfg.edge : nullptr;
         a.limit_ns = cfg.limit_ns ? cfg.limit_ns : wait_limit_ns();
         a.alpha = alpha_used;
         a.dir = cfg.direction;
@@ -939,7 +971,7 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
             a.ctrl = ctrls + bi;
             a.trace = (trace_on && bi == todo.front()) ? trace_buf.as<unsigned long long>() : nullptr;
             void *args[] = {&a};
-            NK_CUDA(cudaLaunchCooperativeKernel((const void *)k_batch<W>, dim3(grid), dim3(kThreads), args, 0, s));
+            NK_CUDA(cudaLaunchCooperativeKernel(kfn, dim3(grid), dim3(kThreads), args, 0, s));
             ::nk::count_launch();
         }
         if (cfg.time_kernels) NK_CUDA(cudaEventRecord(e1, s));
@@ -1066,6 +1098,7 @@ int enqueue_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scor
     a.far = cfg.far;
     a.reach = cfg.reach;
     a.backward = cfg.backward ? 1 : 0;
+    a.edge = nullptr;  // the captured form serves vertex scores only
     a.limit_ns = cfg.limit_ns ? cfg.limit_ns : wait_limit_ns();
     a.alpha = cfg.alpha > 0 ? cfg.alpha : 1.0;
     a.dir = cfg.direction;
@@ -1086,7 +1119,7 @@ int enqueue_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scor
         a.nsrc = std::min(B, k - bi * B);
         a.ctrl = ctrls + bi;
         void *args[] = {&a};
-        NK_CUDA(cudaLaunchKernelExC(&lc, (const void *)k_batch<W>, args));
+        NK_CUDA(cudaLaunchKernelExC(&lc, (const void *)k_batch<W, false>, args));
         ::nk::count_launch();
     }
     *ctrls_out = ctrls;

@@ -312,6 +312,104 @@ int closeness_entry(const nk_graph *gc, bool sample, uint64_t seed, int32_t k, d
     return NK_OK;
 }
 
+// Edge scores from per-arc sums: arc j = (u, v) gets scale * (arc[j] + arc[reverse of j]),
+// so both arcs of an edge hold the same value.  The row u of j and the reverse arc are
+// found by binary search (rows are sorted); a missing reverse arc sets *bad.
+__global__ void k_finish_edges(const int32_t *rp, const int32_t *col, int32_t n, int64_t A,
+                               const double *arc, double scale, double *out, int *bad)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < A;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        int32_t lo = 0, hi = n;  // last u with rp[u] <= j
+        while (hi - lo > 1) {
+            const int32_t mid = lo + (hi - lo) / 2;
+            if ((int64_t)__ldg(rp + mid) <= j) lo = mid; else hi = mid;
+        }
+        const int32_t u = lo, v = __ldg(col + j);
+        int64_t b = __ldg(rp + v), e = __ldg(rp + v + 1);
+        while (b < e) {
+            const int64_t mid = b + (e - b) / 2;
+            if (__ldg(col + mid) < u) b = mid + 1; else e = mid;
+        }
+        if (b >= __ldg(rp + v + 1) || __ldg(col + b) != u) {
+            atomicExch(bad, 1);
+            continue;
+        }
+        out[j] = scale * (arc[j] + arc[b]);
+    }
+}
+
+// Edge betweenness entry: all vertices (exact, scale 1/2) or k sampled sources (scale n/(2k)).
+int edge_entry(const nk_graph *gc, bool sample, uint64_t seed, int32_t k, double *edge_scores,
+               const nk_run_opts *opts)
+{
+    if (!gc) return set_error(NK_ERR_ARG, "graph is null");
+    if (!edge_scores) return set_error(NK_ERR_ARG, "edge_scores is null");
+    nk_graph *g = const_cast<nk_graph *>(gc);
+    const int32_t n = g->n;
+    const int64_t A = g->A;
+    if (sample && (k < 1 || k > n)) return set_error(NK_ERR_ARG, "need 1 <= k <= n (k=%d, n=%d)", k, n);
+    if (!sample) k = n;
+    RunCfg cfg = cfg_of(opts, g);
+    NK_TRY(check_cfg(cfg));
+    const bool dev = opts && (opts->flags & NK_RUN_DEVICE_PTRS);
+    cudaStream_t s = stream();
+    std::lock_guard<std::mutex> lock(g->mu);
+    Tmp dsrc, arc, vsc, hout, flag;
+    NK_TRY(dsrc.alloc(sizeof(int32_t) * k, s));
+    if (sample) {
+        NK_TRY(sample_sources_device(n, seed, k, dsrc.as<int32_t>(), s));
+    } else {
+        k_iota<<<std::max(1, std::min((k + 255) / 256, 8 * num_sms())), 256, 0, s>>>(dsrc.as<int32_t>(), k);
+        ::nk::count_launch();
+    }
+    const size_t arc_bytes = sizeof(double) * (size_t)std::max<int64_t>(A, 1);
+    NK_TRY(arc.alloc(arc_bytes, s));
+    NK_TRY(vsc.alloc(sizeof(double) * (size_t)n, s));
+    NK_TRY(flag.alloc(sizeof(int), s));
+    auto zero = [&]() -> int {
+        NK_CUDA(cudaMemsetAsync(arc.p, 0, arc_bytes, s));
+        NK_CUDA(cudaMemsetAsync(vsc.p, 0, sizeof(double) * (size_t)n, s));
+        return NK_OK;
+    };
+    NK_TRY(zero());
+    NK_CUDA(cudaMemsetAsync(flag.p, 0, sizeof(int), s));
+    cfg.edge = arc.as<double>();
+    t_stats = RunStats();
+    int mode = cfg.mode == NK_MODE_AUTO ? (k >= 16 ? NK_MODE_BATCHED : NK_MODE_PER_SOURCE) : cfg.mode;
+    int rc;
+    if (mode == NK_MODE_BATCHED) {
+        rc = run_batched(g, dsrc.as<int32_t>(), k, vsc.as<double>(), cfg, &t_stats, s);
+        if (rc == NK_ERR_NOMEM && cfg.mode == NK_MODE_AUTO) {
+            NK_TRY(zero());
+            t_stats = RunStats();
+            rc = run_per_source(g, dsrc.as<int32_t>(), k, vsc.as<double>(), cfg, &t_stats, s);
+        }
+    } else {
+        rc = run_per_source(g, dsrc.as<int32_t>(), k, vsc.as<double>(), cfg, &t_stats, s);
+    }
+    NK_TRY(rc);
+    double *dout = edge_scores;
+    if (!dev) {
+        NK_TRY(hout.alloc(arc_bytes, s));
+        dout = hout.as<double>();
+    }
+    const double scale = sample ? (double)n / (2.0 * (double)k) : 0.5;
+    if (A > 0) {
+        const int64_t blocks = std::min<int64_t>((A + 255) / 256, 16LL * num_sms());
+        k_finish_edges<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, s>>>(
+            g->rp.as<int32_t>(), g->col.as<int32_t>(), n, A, arc.as<double>(), scale, dout, flag.as<int>());
+        ::nk::count_launch();
+        NK_CUDA(cudaGetLastError());
+    }
+    int hbad = 0;
+    NK_CUDA(cudaMemcpyAsync(&hbad, flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (!dev && A > 0) NK_CUDA(cudaMemcpyAsync(edge_scores, dout, sizeof(double) * (size_t)A, cudaMemcpyDeviceToHost, s));
+    NK_CUDA(cudaStreamSynchronize(s));
+    if (hbad) return set_error(NK_ERR_GRAPH, "an arc has no reverse arc: the graph is not symmetric");
+    return NK_OK;
+}
+
 }  // namespace
 }  // namespace nk
 
@@ -343,6 +441,17 @@ int nk_betweenness_sources(const nk_graph *g, const int32_t *src, int32_t k, dou
 {
     if (!src) return set_error(NK_ERR_ARG, "src is null");
     return bc_entry(g, src, k, false, 0, scale, scores, opts);
+}
+
+int nk_edge_betweenness_exact(const nk_graph *g, double *edge_scores)
+{
+    return edge_entry(g, false, 0, 0, edge_scores, nullptr);
+}
+
+int nk_edge_betweenness_sampled(const nk_graph *g, uint64_t seed, int32_t k, double *edge_scores,
+                                const nk_run_opts *opts)
+{
+    return edge_entry(g, true, seed, k, edge_scores, opts);
 }
 
 int nk_closeness_exact(const nk_graph *g, double *far, double *reach)

@@ -179,6 +179,7 @@ struct RunCfg {
     bool backward = true;  // false: forward sweep only
     unsigned long long *far = nullptr;    // closeness distance sums (device), or null
     unsigned long long *reach = nullptr;  // closeness reach counts (device), or null
+    double *edge = nullptr;               // edge betweenness: per-arc sums (device, A), or null
 };
 
 inline DevBuf *scratch(const RunCfg &c, nk_graph *g);

@@ -59,6 +59,7 @@ struct SrcArgs {
     double alpha;
     int dir;
     int forward_only;
+    double *edge;        // [A] per-arc shares sigma_v * psi_w (edge betweenness), or null
     // rows longer than kHeavyChunk: chunk table and per-chunk partial sums
     const int32_t *hv, *hfirst, *chunk_h;
     int32_t H, C;
@@ -225,12 +226,13 @@ __device__ void bu_heavy_finish(const SrcArgs &a, int d, int *s_cnt, unsigned lo
 // psi_v = 1/sigma_v + acc and delta_v = sigma_v * acc (Brandes' recurrence with sigma_v
 // factored out), in double-single arithmetic; psi overwrites sigma, delta goes to the
 // FP64 score.
-__device__ __forceinline__ void finish_vertex(const SrcArgs &a, int v, dev::ff acc)
+// Level 0 (the source) is finished only for edge betweenness and gets no score.
+__device__ __forceinline__ void finish_vertex(const SrcArgs &a, int v, dev::ff acc, int d)
 {
     const dev::ff sv = dev::ff_from_u64(dev::ldcg(a.sp + v));
     const dev::ff delta = dev::ff_mul(sv, acc);
     a.sp[v] = dev::ff_pack(dev::ff_add(dev::ff_rcp(sv), acc));
-    if (delta.hi != 0.0f) a.scores[v] += dev::ff_to_double(delta);
+    if (delta.hi != 0.0f && d > 0) a.scores[v] += dev::ff_to_double(delta);
 }
 
 // ------------------------------------------------------------------ backward level d
@@ -250,14 +252,21 @@ __device__ void back_level(const SrcArgs &a, int d, int qo, int nd)
         }
         dev::ff acc = dev::ff_zero();
         if (v >= 0) {
+            // edge betweenness: the arc (v, w) carries sigma_v * psi_w = sigma_v / sigma_w *
+            // (1 + delta_w), read before v's own psi replaces sigma_v
+            const dev::ff sv = a.edge ? dev::ff_from_u64(dev::ldcg(a.sp + v)) : dev::ff_zero();
             const int beg = __ldg(a.rp + v), end = __ldg(a.rp + v + 1);
             for (int j = beg + L.lg; j < end; j += TPV) {
                 const int w = __ldg(a.col + j);
-                if (dev::ldcg(a.dist + w) == d + 1) acc = dev::ff_add(acc, dev::ff_unpack(dev::ldcg(a.sp + w)));
+                if (dev::ldcg(a.dist + w) == d + 1) {
+                    const dev::ff psi = dev::ff_unpack(dev::ldcg(a.sp + w));
+                    acc = dev::ff_add(acc, psi);
+                    if (a.edge) a.edge[j] += dev::ff_to_double(dev::ff_mul(sv, psi));
+                }
             }
         }
         acc = dev::group_sum_ff<TPV>(acc);
-        if (v >= 0 && L.lg == 0) finish_vertex(a, v, acc);
+        if (v >= 0 && L.lg == 0) finish_vertex(a, v, acc, d);
     }
     // heavy vertices of level d: per-chunk partial sums of psi
     for (long long c = L.wid; c < a.C; c += L.nw) {
@@ -265,9 +274,14 @@ __device__ void back_level(const SrcArgs &a, int d, int qo, int nd)
         chunk_of(a, c, h, j0, j1);
         if (dev::ldcg(a.dist + h) != d) continue;
         dev::ff acc = dev::ff_zero();
+        const dev::ff sv = a.edge ? dev::ff_from_u64(dev::ldcg(a.sp + h)) : dev::ff_zero();
         for (int j = j0 + L.lane; j < j1; j += 32) {
             const int w = __ldg(a.col + j);
-            if (dev::ldcg(a.dist + w) == d + 1) acc = dev::ff_add(acc, dev::ff_unpack(dev::ldcg(a.sp + w)));
+            if (dev::ldcg(a.dist + w) == d + 1) {
+                const dev::ff psi = dev::ff_unpack(dev::ldcg(a.sp + w));
+                acc = dev::ff_add(acc, psi);
+                if (a.edge) a.edge[j] += dev::ff_to_double(dev::ff_mul(sv, psi));
+            }
         }
         acc = dev::group_sum_ff<32>(acc);
         if (L.lane == 0) a.part[c] = dev::ff_pack(acc);
@@ -284,7 +298,7 @@ __device__ void back_heavy_finish(const SrcArgs &a, int d)
         dev::ff acc = dev::ff_zero();
         for (int c = __ldg(a.hfirst + i); c < __ldg(a.hfirst + i + 1); ++c)
             acc = dev::ff_add(acc, dev::ff_unpack(dev::ldcg(a.part + c)));
-        finish_vertex(a, h, acc);
+        finish_vertex(a, h, acc, d);
     }
 }
 
@@ -364,7 +378,8 @@ __global__ void __launch_bounds__(kThreads) k_source(SrcArgs a)
     }
     if (ovf) atomicOr(&a.ctrl->ovf, 1);
     if (a.forward_only) return;
-    for (int l = D; l >= 1; --l) {
+    // edge betweenness also sweeps level 0: the source's arcs carry shares
+    for (int l = D; l >= (a.edge ? 0 : 1); --l) {
         back_level<TPV>(a, l, dev::ldcg(a.qoff + l), dev::ldcg(a.cnt + l));
         if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
         if (a.H > 0) {
@@ -473,6 +488,7 @@ int run(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores, const Ru
     a.alpha = cfg.alpha > 0 ? cfg.alpha : 1.0;
     a.dir = cfg.direction;
     a.forward_only = forward_only ? 1 : 0;
+    a.edge = forward_only ? nullptr : cfg.edge;
     a.hv = g->heavy[0].as<int32_t>();
     a.hfirst = g->heavy[1].as<int32_t>();
     a.chunk_h = g->heavy[2].as<int32_t>();

@@ -93,6 +93,8 @@ SIGNATURES = {
     "nk_betweenness_sampled": (_INT, [_P, _U64, _I32, _P]),
     "nk_betweenness_sampled_opts": (_INT, [_P, _U64, _I32, _P, _P]),
     "nk_betweenness_sources": (_INT, [_P, _P, _I32, _D, _P, _P]),
+    "nk_edge_betweenness_exact": (_INT, [_P, _P]),
+    "nk_edge_betweenness_sampled": (_INT, [_P, _U64, _I32, _P, _P]),
     "nk_closeness_exact": (_INT, [_P, _P, _P]),
     "nk_closeness_sampled": (_INT, [_P, _U64, _I32, _P, _P, _P]),
     "nk_last_run_stats": (_INT, [_P]),
@@ -324,6 +326,37 @@ def betweenness_sources(g: Graph, src, scale: float, opts: RunOpts | None = None
     _check(lib().nk_betweenness_sources(g.handle, sp, k, scale, ptr,
                                          ctypes.byref(o) if o is not None else None))
     return res
+
+
+def _arc_count(g: Graph) -> int:
+    return g.info()[1]
+
+
+def edge_betweenness_exact(g: Graph) -> np.ndarray:
+    """Edge betweenness per arc of the canonical CSR (both arcs of an edge equal)."""
+    out = np.empty(max(_arc_count(g), 1), np.float64)
+    _check(lib().nk_edge_betweenness_exact(g.handle, _np_ptr(out)))
+    return out[:_arc_count(g)]
+
+
+def edge_betweenness_sampled(g: Graph, seed: int, k: int, opts: RunOpts | None = None, out=None):
+    """Sampled edge betweenness per arc (scale n/(2k)); out: None (new host array) or a
+    float64 CUDA tensor of A entries."""
+    A = _arc_count(g)
+    if out is not None:
+        if not _is_torch(out) or out.numel() != A:
+            raise ValueError("out must be a CUDA tensor of A entries")
+        o = run_opts() if opts is None else RunOpts.from_buffer_copy(opts)
+        o.flags |= RUN_DEVICE_PTRS
+        _check(lib().nk_edge_betweenness_sampled(g.handle, seed, k, _dev_ptr(out), ctypes.byref(o)))
+        return out
+    res = np.empty(max(A, 1), np.float64)
+    if opts is not None and (opts.flags & RUN_DEVICE_PTRS):
+        opts = RunOpts.from_buffer_copy(opts)
+        opts.flags &= ~RUN_DEVICE_PTRS
+    _check(lib().nk_edge_betweenness_sampled(g.handle, seed, k, _np_ptr(res),
+                                             ctypes.byref(opts) if opts is not None else None))
+    return res[:A]
 
 
 def closeness_exact(g: Graph):

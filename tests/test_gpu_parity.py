@@ -344,3 +344,47 @@ def test_closeness_device_outputs(nk):
     reach = torch.full((n,), -1.0, dtype=torch.float64, device="cuda")
     nk.closeness_sampled(g, 6, 200, nk.run_opts(mode=2, batch=128), out=(far, reach))
     assert np.array_equal(far.cpu().numpy(), f0) and np.array_equal(reach.cpu().numpy(), r0)
+
+
+# ------------------------------------------------------------------ edge betweenness (Section 4.3)
+@pytest.mark.parametrize("name", ["path", "star", "cycle_even", "k_ab", "grid", "tree", "components",
+                                  "isolated", "hubs", "hub_path", "star_big"])
+def test_edge_betweenness_exact_small(nk, name):
+    g, rp, col = both(nk, SMALL[name])
+    want = oracle.edge_betweenness_exact(rp, col)
+    assert close(nk.edge_betweenness_exact(g), want)
+    n = len(rp) - 1
+    for m in MODES:
+        got = nk.edge_betweenness_sampled(g, 3, n, nk.run_opts(**m))
+        assert close(got, want), (name, m)
+
+
+def test_edge_betweenness_sampled_generated(nk):
+    for kind, size, params, k in (("rmat", 13, {}, 300), ("ba", 20000, dict(m0=4), 200),
+                                  ("er", 2000, dict(avg_deg=8.0), 2000)):
+        g = nk.graph_generate(kind, size, 5, **params)
+        n, rp, col = oracle.generate(kind, size, 5, **params)
+        want = oracle.edge_betweenness_sampled(rp, col, 8, k)
+        for m in (dict(), dict(mode=2, batch=128), dict(mode=1)):
+            assert close(nk.edge_betweenness_sampled(g, 8, k, nk.run_opts(**m)), want), (kind, m)
+
+
+def test_edge_betweenness_deep_and_overflow(nk):
+    gp, rp, col = both(nk, G.path(3000))   # deeper than the level slabs: per-source fallback
+    want = oracle.edge_betweenness_sampled(rp, col, 4, 70)
+    assert close(nk.edge_betweenness_sampled(gp, 4, 70, nk.run_opts(mode=2, batch=64)), want)
+    g2, _, _ = both(nk, G.grid(35, 35))
+    for opts in (nk.run_opts(mode=1), nk.run_opts(mode=2, batch=64)):
+        with pytest.raises(nk.NkError) as e:
+            nk.edge_betweenness_sampled(g2, 1, 1225, opts)
+        assert e.value.rc == nk.ERR_OVERFLOW
+
+
+def test_edge_betweenness_device_output(nk):
+    import torch
+    g = nk.graph_generate("rmat", 12, 7)
+    n, rp, col = oracle.generate("rmat", 12, 7)
+    want = oracle.edge_betweenness_sampled(rp, col, 2, 256)
+    out = torch.full((len(col),), -1.0, dtype=torch.float64, device="cuda")
+    nk.edge_betweenness_sampled(g, 2, 256, nk.run_opts(mode=2, batch=256), out=out)
+    assert close(out.cpu().numpy(), want)
