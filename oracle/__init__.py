@@ -5,7 +5,8 @@ reference leg of ``bench.py`` are the only callers.  The product library never i
 this package, and this package never imports the product library.
 
 Every function mirrors one C function and cites the passage of the paper it follows:
-Brandes' algorithm and the sampled estimate (Section 3.2, Table 1), BFS for unweighted
+Brandes' algorithm, the sampled estimate and the error-bounded estimate after Riondato
+and Kornaropoulos (Section 3.2, Table 1), BFS for unweighted
 graphs (Section 3.4), edge betweenness (Section 4.3), closeness exact and sampled (Table 1),
 the generators of Section 5 (Table 2).
 """
@@ -69,6 +70,10 @@ def _load():
             "or_betweenness_sampled": (ctypes.c_int, [i32, P, P, u64, i32, P]),
             "or_closeness": (ctypes.c_int, [i32, P, P, i32, P, dbl, P, P]),
             "or_edge_betweenness": (ctypes.c_int, [i32, P, P, i32, P, dbl, P]),
+            "or_vertex_diameter_estimate": (ctypes.c_int, [i32, P, P, P]),
+            "or_rk_sample_count": (i64, [dbl, dbl, i32]),
+            "or_rk_path": (i32, [i32, P, P, u64, i64, P, P]),
+            "or_betweenness_rk": (ctypes.c_int, [i32, P, P, dbl, dbl, u64, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -240,6 +245,52 @@ def edge_betweenness_exact(rp, col) -> np.ndarray:
 def edge_betweenness_sampled(rp, col, seed: int, k: int) -> np.ndarray:
     n = len(rp) - 1
     return edge_betweenness_sources(rp, col, sample_sources(n, seed, k), n / (2.0 * k))
+
+
+# ---------------------------------------------------------------- error-bounded estimate (Section 3.2)
+def vertex_diameter_estimate(rp, col) -> int:
+    """Upper bound on the vertices of a shortest path: per component, min(|C|, 2 ecc(x) + 1)
+    with x its smallest vertex; the largest over the components."""
+    rp, col = _i32(rp), _i32(col)
+    vd = ctypes.c_int32()
+    rc = _load().or_vertex_diameter_estimate(len(rp) - 1, _p(rp), _p(col), ctypes.byref(vd))
+    if rc:
+        raise OracleError(rc, "vertex_diameter_estimate")
+    return vd.value
+
+
+def rk_sample_count(eps: float, delta: float, vd: int) -> int:
+    r = _load().or_rk_sample_count(eps, delta, vd)
+    if r < 0:
+        raise OracleError(r, "rk_sample_count")
+    return int(r)
+
+
+def rk_path(rp, col, seed: int, i: int):
+    """(u, v, interior) of sample i: the ordered pair and the interior vertices of its path
+    from v towards u (None if v is not reachable from u)."""
+    rp, col = _i32(rp), _i32(col)
+    n = len(rp) - 1
+    path = np.empty(n, np.int32)
+    uv = np.empty(2, np.int32)
+    L = _load().or_rk_path(n, _p(rp), _p(col), seed, i, _p(uv), _p(path))
+    if L < -1:
+        raise OracleError(L, "rk_path")
+    return int(uv[0]), int(uv[1]), (None if L == -1 else path[:L].copy())
+
+
+def betweenness_rk(rp, col, eps: float, delta: float, seed: int):
+    """(scores, r, vd): the Riondato-Kornaropoulos estimate on the scale of the exact
+    unordered scores."""
+    rp, col = _i32(rp), _i32(col)
+    n = len(rp) - 1
+    out = np.empty(n, np.float64)
+    r, vd = ctypes.c_int64(), ctypes.c_int32()
+    rc = _load().or_betweenness_rk(n, _p(rp), _p(col), eps, delta, seed, _p(out),
+                                   ctypes.byref(r), ctypes.byref(vd))
+    if rc:
+        raise OracleError(rc, "betweenness_rk")
+    return out, r.value, vd.value
 
 
 # ---------------------------------------------------------------- closeness (Table 1)

@@ -526,6 +526,164 @@ int or_edge_betweenness(int32_t n, const int32_t *row_ptr, const int32_t *col, i
 }
 
 /* ------------------------------------------------------------------------------ */
+/* Betweenness with an error bound (Section 3.2, citing Riondato and Kornaropoulos): */
+/* r random pairs, one uniformly chosen shortest path per pair, every interior      */
+/* vertex of the path counted once; with r from the vertex-diameter bound below,    */
+/* every normalised estimate is within epsilon of the exact value with probability */
+/* at least 1 - delta.                                                              */
+/*   vertex diameter bound: per connected component C, a BFS from its smallest      */
+/*     vertex x gives ecc(x); a shortest path has at most min(|C|, 2 ecc(x) + 1)    */
+/*     vertices; VD = the largest bound over the components;                        */
+/*   r = ceil(0.5 / eps^2 * (floor(log2(max(VD - 2, 1))) + 1 + ln(1 / delta)));     */
+/*   pair i: u = below(stream(seed, 3i), n), v = below(stream(seed, 3i+1), n-1),    */
+/*     v += (v >= u) (an ordered pair of distinct vertices);                        */
+/*   path of pair i, walked back from v with key = stream(seed, 3i+2): at step j    */
+/*     from w, t = below(stream(key, j), sigma[w]); the predecessors z of w (in    */
+/*     adjacency order) split [0, sigma[w]) into runs of length sigma[z]; the run   */
+/*     holding t names the next vertex (probability sigma[z] / sigma[w]);           */
+/*   scores[w] = count[w] * n (n - 1) / (2 r): the estimate on the scale of the     */
+/*     exact unordered scores (the normalised value is scores * 2 / (n (n - 1))).   */
+/* ------------------------------------------------------------------------------ */
+
+int or_vertex_diameter_estimate(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                                int32_t *vd)
+{
+    if (n < 1) return OR_ERR_ARG;
+    int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    if (!dist || !queue) { free(dist); free(queue); return OR_ERR_NOMEM; }
+    for (int32_t v = 0; v < n; ++v) dist[v] = -1;
+    int32_t best = 0;
+    for (int32_t x = 0; x < n; ++x) {
+        if (dist[x] >= 0) continue;
+        int32_t head = 0, tail = 0, ecc = 0;
+        dist[x] = 0;
+        queue[tail++] = x;
+        while (head < tail) {
+            int32_t v = queue[head++];
+            if (dist[v] > ecc) ecc = dist[v];
+            for (int32_t j = row_ptr[v]; j < row_ptr[v + 1]; ++j)
+                if (dist[col[j]] < 0) {
+                    dist[col[j]] = dist[v] + 1;
+                    queue[tail++] = col[j];
+                }
+        }
+        int64_t bound = 2 * (int64_t)ecc + 1;
+        if (bound > tail) bound = tail; /* tail = |C| */
+        if (bound > best) best = (int32_t)bound;
+    }
+    free(dist);
+    free(queue);
+    *vd = best;
+    return OR_OK;
+}
+
+int64_t or_rk_sample_count(double eps, double delta, int32_t vd)
+{
+    if (!(eps > 0.0 && eps < 1.0) || !(delta > 0.0 && delta < 1.0) || vd < 1) return OR_ERR_ARG;
+    int64_t x = vd - 2 < 1 ? 1 : (int64_t)vd - 2;
+    int lg = 0;
+    while ((x >> (lg + 1)) != 0) ++lg; /* floor(log2 x) */
+    double r = ceil(0.5 / (eps * eps) * ((double)lg + 1.0 + log(1.0 / delta)));
+    if (!(r <= 2147483647.0)) return OR_ERR_ARG;
+    return (int64_t)r;
+}
+
+/* The pair (u, v) of sample i and the interior vertices of its path (from v towards
+ * u) into path[]; returns their number, or -1 if v is unreachable from u. */
+static int32_t or_rk_one(int32_t n, const int32_t *row_ptr, const int32_t *col, uint64_t seed,
+                         int64_t i, int32_t *dist, uint64_t *sigma, int32_t *queue,
+                         int32_t *path, int32_t *uv, int *rc)
+{
+    const int32_t u = (int32_t)or_below(or_stream(seed, 3 * (uint64_t)i), (uint64_t)n);
+    int32_t v = (int32_t)or_below(or_stream(seed, 3 * (uint64_t)i + 1), (uint64_t)(n - 1));
+    if (v >= u) ++v;
+    if (uv) { uv[0] = u; uv[1] = v; }
+    for (int32_t x = 0; x < n; ++x) { dist[x] = -1; sigma[x] = 0; }
+    dist[u] = 0;
+    sigma[u] = 1;
+    int32_t head = 0, tail = 0;
+    queue[tail++] = u;
+    while (head < tail) {
+        int32_t x = queue[head++];
+        for (int32_t j = row_ptr[x]; j < row_ptr[x + 1]; ++j) {
+            int32_t w = col[j];
+            if (dist[w] < 0) {
+                dist[w] = dist[x] + 1;
+                queue[tail++] = w;
+            }
+            if (dist[w] == dist[x] + 1 && __builtin_add_overflow(sigma[w], sigma[x], &sigma[w]))
+                *rc = OR_ERR_OVERFLOW;
+        }
+    }
+    if (dist[v] < 0) return -1;
+    const uint64_t key = or_stream(seed, 3 * (uint64_t)i + 2);
+    int32_t w = v, len = 0;
+    for (uint64_t step = 0; dist[w] > 1; ++step) {
+        const uint64_t t = or_below(or_stream(key, step), sigma[w]);
+        uint64_t run = 0;
+        int32_t z = -1;
+        for (int32_t j = row_ptr[w]; j < row_ptr[w + 1]; ++j) {
+            int32_t c = col[j];
+            if (dist[c] != dist[w] - 1) continue;
+            run += sigma[c];
+            if (t < run) { z = c; break; }
+        }
+        if (z < 0) { *rc = OR_ERR_GRAPH; return -1; }
+        path[len++] = z;
+        w = z;
+    }
+    return len;
+}
+
+/* The pair of sample i (uv[0] = u, uv[1] = v) and the interior vertices of its path
+ * (for tests of the pair and path laws). */
+int32_t or_rk_path(int32_t n, const int32_t *row_ptr, const int32_t *col, uint64_t seed,
+                   int64_t i, int32_t *uv, int32_t *path)
+{
+    if (n < 2 || i < 0) return OR_ERR_ARG;
+    int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    uint64_t *sigma = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
+    int rc = OR_OK;
+    int32_t len = -1;
+    if (dist && queue && sigma) len = or_rk_one(n, row_ptr, col, seed, i, dist, sigma, queue, path, uv, &rc);
+    else rc = OR_ERR_NOMEM;
+    free(dist); free(queue); free(sigma);
+    return rc != OR_OK ? rc : len;
+}
+
+int or_betweenness_rk(int32_t n, const int32_t *row_ptr, const int32_t *col, double eps,
+                      double delta, uint64_t seed, double *scores, int64_t *r_out, int32_t *vd_out)
+{
+    int32_t vd = 0;
+    int rc = or_vertex_diameter_estimate(n, row_ptr, col, &vd);
+    if (rc != OR_OK) return rc;
+    const int64_t r = or_rk_sample_count(eps, delta, vd);
+    if (r < 0) return (int)r;
+    *r_out = r;
+    *vd_out = vd;
+    for (int32_t v = 0; v < n; ++v) scores[v] = 0.0;
+    if (n < 2) return OR_OK;
+    int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *path = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    uint64_t *sigma = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
+    uint64_t *count = (uint64_t *)calloc((size_t)n, sizeof(uint64_t));
+    if (!dist || !queue || !path || !sigma || !count) rc = OR_ERR_NOMEM;
+    for (int64_t i = 0; rc == OR_OK && i < r; ++i) {
+        int32_t len = or_rk_one(n, row_ptr, col, seed, i, dist, sigma, queue, path, NULL, &rc);
+        for (int32_t p = 0; rc == OR_OK && p < len; ++p) count[path[p]] += 1;
+    }
+    if (rc == OR_OK) {
+        const double scale = (double)n * (double)(n - 1) / (2.0 * (double)r);
+        for (int32_t v = 0; v < n; ++v) scores[v] = (double)count[v] * scale;
+    }
+    free(dist); free(queue); free(path); free(sigma); free(count);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------------ */
 /* Closeness (Table 1: "closeness", shortest-path search from each node, and its    */
 /* approximation after Eppstein and Wang with s sampled sources).  For every vertex */
 /* v:  far[v] = scale * sum of d(s, v) over the sources s != v that reach v,        */

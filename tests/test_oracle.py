@@ -604,3 +604,102 @@ def test_edge_betweenness_sampled_unbiased_and_k_equals_n():
     mean, se = runs.mean(0), runs.std(0, ddof=1) / np.sqrt(len(runs))
     z = np.abs(mean - e) / np.maximum(se, 1e-12)
     assert np.mean(z < 4) > 0.99
+
+
+# ------------------------------------------------------------------ error-bounded estimate (Section 3.2)
+def test_vertex_diameter_estimate_closed_forms():
+    for n in (1, 2, 7, 30):
+        _, rp, col = csr(G.path(n))
+        assert oracle.vertex_diameter_estimate(rp, col) == n      # 2(n-1)+1 capped by |C| = n
+    _, rp, col = csr(G.star(9))
+    assert oracle.vertex_diameter_estimate(rp, col) == 3          # from the centre: ecc 1
+    _, rp, col = csr(G.cycle(11))
+    assert oracle.vertex_diameter_estimate(rp, col) == 11         # ecc 5 -> 11 = |C|
+    _, rp, col = csr(G.grid(4, 6))
+    assert oracle.vertex_diameter_estimate(rp, col) == 17         # corner ecc 8 -> 17 <= 24
+    _, rp, col = csr(G.disjoint_union(G.star(5), G.path(9), G.complete(1)))
+    assert oracle.vertex_diameter_estimate(rp, col) == 9          # the largest component bound
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_vertex_diameter_estimate_bounds(seed):
+    g = G.gnp(40, 0.06 + 0.02 * seed, seed) if seed % 2 else G.random_tree(40, seed)
+    n, rp, col = csr(g)
+    d = floyd_warshall(*g)
+    vd_true = int(d.max()) + 1                                   # vertices on a longest shortest path
+    vd = oracle.vertex_diameter_estimate(rp, col)
+    assert vd_true <= vd <= 2 * vd_true + 1
+
+
+def test_rk_sample_count_hand_values():
+    # r = ceil(0.5 / eps^2 * (floor(log2(max(VD - 2, 1))) + 1 + ln(1 / delta))), worked by hand
+    assert oracle.rk_sample_count(0.1, 0.1, 10) == 316     # 50 * (3 + 1 + 2.302585) = 315.13
+    assert oracle.rk_sample_count(0.1, 0.1, 12) == 316     # floor(log2 10) = 3 as well
+    assert oracle.rk_sample_count(0.1, 0.1, 11) == 316
+    assert oracle.rk_sample_count(0.1, 0.1, 18) == 366     # 50 * (4 + 1 + 2.302585) = 365.13
+    assert oracle.rk_sample_count(0.05, 0.01, 3) == 1122   # 200 * (0 + 1 + 4.605170) = 1121.03
+    assert oracle.rk_sample_count(0.2, 0.5, 2) == 22       # 12.5 * (1 + 0.693147) = 21.16
+    with pytest.raises(oracle.OracleError):
+        oracle.rk_sample_count(0.0, 0.1, 5)
+    with pytest.raises(oracle.OracleError):
+        oracle.rk_sample_count(0.1, 1.0, 5)
+
+
+def test_rk_pair_and_path_laws():
+    # 3 x 3 grid: 72 ordered pairs equally likely; between opposite corners the 6 shortest
+    # paths equally likely
+    n, rp, col = csr(G.grid(3, 3))
+    N = 20000
+    pairs, paths = {}, {}
+    for i in range(N):
+        u, v, p = oracle.rk_path(rp, col, 11, i)
+        assert u != v
+        pairs[(u, v)] = pairs.get((u, v), 0) + 1
+        if (u, v) == (0, 8):
+            paths[tuple(p)] = paths.get(tuple(p), 0) + 1
+    assert len(pairs) == 72
+    e = N / 72
+    chi2 = sum((c - e) ** 2 / e for c in pairs.values())
+    assert chi2 < 71 + 5 * math.sqrt(2 * 71)
+    assert len(paths) == 6
+    tot = sum(paths.values())
+    chi2 = sum((c - tot / 6) ** 2 / (tot / 6) for c in paths.values())
+    assert chi2 < 5 + 5 * math.sqrt(10)
+
+
+def test_rk_tree_paths_are_the_tree_paths():
+    n = 60
+    g = G.random_tree(n, 4)
+    _, rp, col = csr(g)
+    for i in range(200):
+        u, v, p = oracle.rk_path(rp, col, 2, i)
+        dist, _ = oracle.bfs(rp, col, u)
+        # walk back from v by decreasing distance: unique in a tree
+        w, want = v, []
+        while dist[w] > 1:
+            w = next(int(c) for c in col[rp[w]:rp[w + 1]] if dist[c] == dist[w] - 1)
+            want.append(w)
+        assert p.tolist() == want
+
+
+def test_rk_unbiased_and_within_epsilon():
+    n, rp, col = oracle.generate("er", 80, 3, avg_deg=4.0)
+    exact = oracle.betweenness_exact(rp, col)
+    eps, delta = 0.05, 0.1
+    runs, misses = [], 0
+    for s in range(60):
+        sc, r, vd = oracle.betweenness_rk(rp, col, eps, delta, s)
+        runs.append(sc)
+        misses += np.max(np.abs(sc - exact)) * 2 / (n * (n - 1)) > eps
+    assert misses <= 6 + 3                                      # P(miss) <= delta = 0.1
+    runs = np.stack(runs)
+    mean, se = runs.mean(0), runs.std(0, ddof=1) / np.sqrt(len(runs))
+    z = np.abs(mean - exact) / np.maximum(se, 1e-12)
+    assert np.mean(z < 4) > 0.97
+
+
+def test_rk_small_vertex_diameter_gives_zero():
+    # complete graph: no shortest path has an interior vertex
+    _, rp, col = csr(G.complete(6))
+    sc, r, vd = oracle.betweenness_rk(rp, col, 0.2, 0.2, 1)
+    assert vd == 3 and r == oracle.rk_sample_count(0.2, 0.2, 3) and np.all(sc == 0)
