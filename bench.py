@@ -488,6 +488,28 @@ def run_ours(args, world, rank, local):
                                    "form": "batched sweeps with per-arc shares, sampled sources, scale n/(2k)"}
         del edge_d
 
+    # ---- error-bounded estimate after Riondato-Kornaropoulos (Section 3.2) on the same graph:
+    #      epsilon 0.01, delta 0.1; r sampled pairs, one forward sweep and one path walk each
+    if not exact and rank == 0:
+        rk_eps, rk_delta = 0.01, 0.1
+        ro = nk.run_opts(mode=nk.MODE_BATCHED, batch=B, alpha=stats["alpha"], flags=nk.RUN_TIME_KERNELS)
+        rk_out = torch.empty(n, dtype=torch.float64, device="cuda")
+        _, rk_r, rk_vd = nk.betweenness_rk(g, rk_eps, rk_delta, sseed, ro, out=rk_out)
+        torch.cuda.synchronize()
+        rms = []
+        for _ in range(max(1, min(args.steps, 3))):
+            flush.zero_()
+            ev0.record(stream)
+            nk.betweenness_rk(g, rk_eps, rk_delta, sseed, ro, out=rk_out)
+            ev1.record(stream)
+            ev1.synchronize()
+            rms.append(ev0.elapsed_time(ev1))
+        rtot = sum(rms)
+        out["rk_estimate"] = {"value": m * rk_r * len(rms) / (rtot / 1e3) / 1e9, "unit": UNIT,
+                              "ms_per_step": rtot / len(rms), "epsilon": rk_eps, "delta": rk_delta,
+                              "samples": rk_r, "vertex_diameter_bound": rk_vd, "batch": B,
+                              "form": "batched forward sweeps + one random path walk per sample"}
+
     # ---- plain per-source form on the same workload (the baseline it beats)
     if not args.no_per_source and rank == 0:
         po = nk.run_opts(mode=nk.MODE_PER_SOURCE, flags=nk.RUN_TIME_KERNELS)

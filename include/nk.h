@@ -194,6 +194,30 @@ int nk_last_run_stats(nk_run_stats *out);
  * calls with batch/alpha = 0 use it). */
 int nk_autotune(const nk_graph *g, uint64_t seed, int32_t k, nk_run_opts *best);
 
+/* ---------------------------------------------------------------- error-bounded estimate (Section 3.2) */
+/* Betweenness with an error bound, after Riondato and Kornaropoulos (cited in Section 3.2 as
+ * the estimate whose scores are within +-epsilon of the exact ones with a user-chosen
+ * probability).  r random ordered pairs (u, v) of distinct vertices; for each, one shortest
+ * u-v path chosen uniformly (if v is reachable); every interior vertex of the path is counted.
+ *   vertex-diameter bound VD (nk_vertex_diameter_estimate): per connected component C with
+ *     smallest vertex x, min(|C|, 2 ecc(x) + 1); the largest over the components;
+ *   r = ceil(0.5 / epsilon^2 * (floor(log2(max(VD - 2, 1))) + 1 + ln(1 / delta)));
+ *   pair i: u = floor(s0 n / 2^64), v = floor(s1 (n-1) / 2^64), v += (v >= u), with s0, s1
+ *     outputs 3i and 3i+1 of the SplitMix64 stream seeded with seed; output 3i+2 seeds the
+ *     path walk: from w (starting at v), step j draws t = floor(x_j sigma_w / 2^64) and
+ *     moves to the predecessor z whose run of length sigma_z, laid end to end in adjacency
+ *     order, holds t;
+ *   scores[w] = count[w] * n (n - 1) / (2 r): on the scale of the exact unordered scores
+ *     (the normalised estimate, which the bound is about, is scores[w] * 2 / (n (n - 1))).
+ * samples and vertex_diameter (nullable) receive r and VD.  scores holds n doubles (device
+ * with NK_RUN_DEVICE_PTRS).  Errors: NK_ERR_ARG (epsilon or delta outside (0, 1), r above
+ * 2^31 - 1, null pointers), NK_ERR_OVERFLOW (a path count above 2^64 - 1), NK_ERR_NOMEM,
+ * NK_ERR_TIMEOUT.  Device memory: 16 r + 8 n bytes besides the sweep's own workspace. */
+int nk_betweenness_rk(const nk_graph *g, double epsilon, double delta, uint64_t seed, double *scores,
+                      int64_t *samples, int32_t *vertex_diameter, const nk_run_opts *opts);
+/* The vertex-diameter bound above (computed once per graph, then cached). */
+int nk_vertex_diameter_estimate(const nk_graph *g, int32_t *vd);
+
 /* ---------------------------------------------------------------- edge betweenness (Section 4.3) */
 /* Edge betweenness: for an edge {u, v}, the sum over unordered reachable pairs {s, t} of the
  * fraction of shortest s-t paths that use the edge (Section 4.3: edge centrality from the

@@ -95,6 +95,11 @@ struct BArgs {
     unsigned long long *reach;   // [n] closeness: number of the batch's sources that reach v
     int backward;                // 0: forward sweep only (closeness)
     double *edge;                // [A] edge betweenness: per-arc shares, or null
+    // error-bounded estimate (forward sweep only): per source slot, the target of its
+    // random shortest path and the key of the walk's stream; counts of interior vertices
+    const int32_t *rk_t;
+    const unsigned long long *rk_key;
+    unsigned long long *rk_count;
 };
 
 template <int W> struct Bits {
@@ -712,6 +717,59 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
         a.ctrl->bu_levels = bu;
     }
     if (ovf) atomicOr(&a.ctrl->ovf, 1);
+    if (a.rk_t) {
+        // error-bounded estimate: one warp per source slot b walks one shortest path back
+        // from its target, choosing each predecessor z of w with probability
+        // sigma_b(z) / sigma_b(w): t = below(stream(key, step), sigma_b(w)) falls in the
+        // run of z when the predecessors' sigma values are laid end to end in adjacency
+        // order.  Every vertex strictly between the source and the target is counted.
+        // The slabs and sigma rows are complete: the last level ended with a grid barrier.
+        const long long wid = tid >> 5, nw = nthr >> 5;
+        for (long long b = wid; b < a.nsrc; b += nw) {
+            const int v = __ldg(a.rk_t + b);
+            const int q = (int)(b >> 6);
+            const unsigned long long bit = 1ull << (b & 63);
+            int L = -1;
+            for (int l0 = 1; l0 <= D && L < 0; l0 += 32) {
+                const int l = l0 + lane;
+                const bool hit = l <= D && (__ldcg(a.F + (size_t)l * slab + (size_t)v * W + q) & bit) != 0;
+                const unsigned m = __ballot_sync(FULL, hit);
+                if (m) L = l0 + __ffs(m) - 1;
+            }
+            if (L < 0) continue;  // the target is not reachable from the source
+            const unsigned long long key = __ldg(a.rk_key + b);
+            int w = v;
+            for (int l = L, step = 0; l > 1; --l, ++step) {
+                const unsigned long long sw = __ldcg(a.sp + (size_t)w * B + b);
+                const unsigned long long t = dev::below(dev::stream_at(key, (uint64_t)step), sw);
+                const unsigned long long *Fp = a.F + (size_t)(l - 1) * slab;
+                const int end = __ldg(a.rp + w + 1);
+                unsigned long long run = 0;
+                int z = -1;
+                for (int base = __ldg(a.rp + w); base < end && z < 0; base += 32) {
+                    const int j = base + lane;
+                    int c = -1;
+                    unsigned long long x = 0;
+                    if (j < end) {
+                        c = __ldg(a.col + j);
+                        if (__ldcg(Fp + (size_t)c * W + q) & bit) x = __ldcg(a.sp + (size_t)c * B + b);
+                    }
+                    unsigned long long incl = x;  // inclusive prefix over the lanes
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const unsigned long long y = __shfl_up_sync(FULL, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    const unsigned m = __ballot_sync(FULL, x != 0 && run + incl > t);
+                    if (m) z = __shfl_sync(FULL, c, __ffs(m) - 1);
+                    else run += __shfl_sync(FULL, incl, 31);
+                }
+                if (z < 0) break;  // only with a wrapped path count (reported as an overflow)
+                if (lane == 0) atomicAdd(a.rk_count + z, 1ull);
+                w = z;
+            }
+        }
+    }
     if (a.far) {
         // closeness: v is at distance l from the sources of F_l[v]; one thread per vertex
         // adds its level sums once the whole sweep has stayed within the slabs (a batch
@@ -955,6 +1013,7 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
         a.reach = cfg.reach;
         a.backward = cfg.backward ? 1 : 0;
         a.edge = edge ? cfg.edge : nullptr;
+        a.rk_count = cfg.rk_count;
         a.limit_ns = cfg.limit_ns ? cfg.limit_ns : wait_limit_ns();
         a.alpha = alpha_used;
         a.dir = cfg.direction;
@@ -969,6 +1028,8 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
             a.src = d_src + (size_t)bi * B;
             a.nsrc = std::min(B, k - bi * B);
             a.ctrl = ctrls + bi;
+            a.rk_t = cfg.rk_t ? cfg.rk_t + (size_t)bi * B : nullptr;
+            a.rk_key = cfg.rk_key ? cfg.rk_key + (size_t)bi * B : nullptr;
             a.trace = (trace_on && bi == todo.front()) ? trace_buf.as<unsigned long long>() : nullptr;
             void *args[] = {&a};
             NK_CUDA(cudaLaunchCooperativeKernel(kfn, dim3(grid), dim3(kThreads), args, 0, s));
@@ -1032,6 +1093,10 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
         for (int bi : deep) {
             RunCfg pc = cfg;
             pc.tpv = 0;
+            if (pc.rk_t) {
+                pc.rk_t += (size_t)bi * B;
+                pc.rk_key += (size_t)bi * B;
+            }
             NK_TRY(run_per_source(g, d_src + (size_t)bi * B, std::min(B, k - bi * B), d_scores, pc, st, s));
         }
         return NK_OK;
@@ -1099,6 +1164,9 @@ int enqueue_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scor
     a.reach = cfg.reach;
     a.backward = cfg.backward ? 1 : 0;
     a.edge = nullptr;  // the captured form serves vertex scores only
+    a.rk_t = nullptr;
+    a.rk_key = nullptr;
+    a.rk_count = nullptr;
     a.limit_ns = cfg.limit_ns ? cfg.limit_ns : wait_limit_ns();
     a.alpha = cfg.alpha > 0 ? cfg.alpha : 1.0;
     a.dir = cfg.direction;

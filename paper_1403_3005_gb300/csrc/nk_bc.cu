@@ -410,6 +410,77 @@ int edge_entry(const nk_graph *gc, bool sample, uint64_t seed, int32_t k, double
     return NK_OK;
 }
 
+__global__ void k_rk_scale(const unsigned long long *count, int32_t n, double scale, double *out)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        out[v] = (double)count[v] * scale;
+}
+
+// Error-bounded estimate entry: r pairs from the vertex-diameter bound, one forward sweep
+// per pair's source (batched: B pairs per launch), one random path walked back from each
+// target, counts scaled by n (n - 1) / (2 r).
+int rk_entry(const nk_graph *gc, double eps, double delta, uint64_t seed, double *scores,
+             int64_t *samples_out, int32_t *vd_out, const nk_run_opts *opts)
+{
+    if (!gc) return set_error(NK_ERR_ARG, "graph is null");
+    if (!scores) return set_error(NK_ERR_ARG, "scores is null");
+    if (!(eps > 0.0 && eps < 1.0) || !(delta > 0.0 && delta < 1.0))
+        return set_error(NK_ERR_ARG, "need 0 < epsilon < 1 and 0 < delta < 1");
+    nk_graph *g = const_cast<nk_graph *>(gc);
+    const int32_t n = g->n;
+    RunCfg cfg = cfg_of(opts, g);
+    NK_TRY(check_cfg(cfg));
+    const bool dev = opts && (opts->flags & NK_RUN_DEVICE_PTRS);
+    cudaStream_t s = stream();
+    std::lock_guard<std::mutex> lock(g->mu);
+    int32_t vd = 0;
+    NK_TRY(vertex_diameter_bound(g, s, &vd));
+    const int64_t r = rk_sample_count(eps, delta, vd);
+    if (r < 0) return set_error(NK_ERR_ARG, "the sample count for epsilon %g, delta %g exceeds 2^31 - 1", eps, delta);
+    if (samples_out) *samples_out = r;
+    if (vd_out) *vd_out = vd;
+    Tmp pairs, cnt, hout;
+    NK_TRY(cnt.alloc(sizeof(unsigned long long) * (size_t)n, s));
+    NK_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * (size_t)n, s));
+    t_stats = RunStats();
+    if (n >= 2) {
+        NK_TRY(pairs.alloc((sizeof(int32_t) * 2 + sizeof(unsigned long long)) * (size_t)r, s));
+        unsigned long long *key = pairs.as<unsigned long long>();
+        int32_t *src = reinterpret_cast<int32_t *>(key + r), *tgt = src + r;
+        NK_TRY(rk_pairs(seed, n, r, src, tgt, key, s));
+        cfg.backward = false;
+        cfg.rk_t = tgt;
+        cfg.rk_key = key;
+        cfg.rk_count = cnt.as<unsigned long long>();
+        const int k = (int)r;
+        int mode = cfg.mode == NK_MODE_AUTO ? (k >= 16 ? NK_MODE_BATCHED : NK_MODE_PER_SOURCE) : cfg.mode;
+        int rc;
+        if (mode == NK_MODE_BATCHED) {
+            rc = run_batched(g, src, k, nullptr, cfg, &t_stats, s);
+            if (rc == NK_ERR_NOMEM && cfg.mode == NK_MODE_AUTO) {
+                NK_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * (size_t)n, s));
+                t_stats = RunStats();
+                rc = run_per_source(g, src, k, nullptr, cfg, &t_stats, s);
+            }
+        } else {
+            rc = run_per_source(g, src, k, nullptr, cfg, &t_stats, s);
+        }
+        NK_TRY(rc);
+    }
+    double *dout = scores;
+    if (!dev) {
+        NK_TRY(hout.alloc(sizeof(double) * (size_t)n, s));
+        dout = hout.as<double>();
+    }
+    const double scale = (double)n * (double)(n - 1) / (2.0 * (double)r);
+    k_rk_scale<<<std::max(1, std::min((n + 255) / 256, 8 * num_sms())), 256, 0, s>>>(cnt.as<unsigned long long>(), n, scale, dout);
+    ::nk::count_launch();
+    NK_CUDA(cudaGetLastError());
+    if (!dev) NK_CUDA(cudaMemcpyAsync(scores, dout, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, s));
+    NK_CUDA(cudaStreamSynchronize(s));
+    return NK_OK;
+}
+
 }  // namespace
 }  // namespace nk
 
@@ -441,6 +512,20 @@ int nk_betweenness_sources(const nk_graph *g, const int32_t *src, int32_t k, dou
 {
     if (!src) return set_error(NK_ERR_ARG, "src is null");
     return bc_entry(g, src, k, false, 0, scale, scores, opts);
+}
+
+int nk_betweenness_rk(const nk_graph *g, double epsilon, double delta, uint64_t seed, double *scores,
+                      int64_t *samples, int32_t *vertex_diameter, const nk_run_opts *opts)
+{
+    return rk_entry(g, epsilon, delta, seed, scores, samples, vertex_diameter, opts);
+}
+
+int nk_vertex_diameter_estimate(const nk_graph *gc, int32_t *vd)
+{
+    if (!gc || !vd) return set_error(NK_ERR_ARG, "graph or output is null");
+    nk_graph *g = const_cast<nk_graph *>(gc);
+    std::lock_guard<std::mutex> lock(g->mu);
+    return vertex_diameter_bound(g, stream(), vd);
 }
 
 int nk_edge_betweenness_exact(const nk_graph *g, double *edge_scores)

@@ -136,9 +136,19 @@ struct nk_graph {
     int32_t heavy_H = -1, heavy_C = 0;
     std::vector<int32_t> h_hv, h_hfirst;  // host copies of heavy[0] and heavy[1]
     nk::CapturedRun captured;             // last call captured with NK_RUN_CUDA_GRAPH
+    int32_t vd_est = -1;                  // cached vertex-diameter bound (nk_rk.cu), -1 = not yet
 };
 
 namespace nk {
+
+// ---------------------------------------------------------------- error-bounded estimate (nk_rk.cu)
+// Upper bound on the vertices of a shortest path (cached on the graph).
+int vertex_diameter_bound(nk_graph *g, cudaStream_t s, int32_t *vd);
+// Samples for error eps with probability 1 - delta, or -1 for bad arguments.
+int64_t rk_sample_count(double eps, double delta, int32_t vd);
+// The r sampled pairs (src -> tgt) and the keys of their path walks.
+int rk_pairs(uint64_t seed, int32_t n, int64_t r, int32_t *src, int32_t *tgt, unsigned long long *key,
+             cudaStream_t s);
 
 // ---------------------------------------------------------------- primitives (nk_core.cu)
 // Exclusive prefix sum of count int64 values (in may equal out); *total (device, may be
@@ -180,6 +190,11 @@ struct RunCfg {
     unsigned long long *far = nullptr;    // closeness distance sums (device), or null
     unsigned long long *reach = nullptr;  // closeness reach counts (device), or null
     double *edge = nullptr;               // edge betweenness: per-arc sums (device, A), or null
+    // error-bounded estimate: per source index i, the target of its random shortest path,
+    // the key of the walk's random stream, and the per-vertex counts of interior vertices
+    const int32_t *rk_t = nullptr;
+    const unsigned long long *rk_key = nullptr;
+    unsigned long long *rk_count = nullptr;
 };
 
 inline DevBuf *scratch(const RunCfg &c, nk_graph *g);

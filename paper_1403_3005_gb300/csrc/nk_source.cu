@@ -389,6 +389,48 @@ __global__ void __launch_bounds__(kThreads) k_source(SrcArgs a)
     }
 }
 
+// error-bounded estimate after a forward sweep from the sample's source (dist, sigma):
+// one warp walks back from the target t, choosing each predecessor z of w with probability
+// sigma[z] / sigma[w] (the run of z holds below(stream(key, step), sigma[w]) when the
+// predecessors' sigma values are laid end to end in adjacency order), and counts every
+// vertex strictly between source and target
+__global__ void k_rk_walk(const int32_t *rp, const int32_t *col, const int32_t *dist,
+                          const unsigned long long *sigma, const int32_t *tgt,
+                          const unsigned long long *key, unsigned long long *count)
+{
+    const int lane = threadIdx.x & 31;
+    int w = *tgt;
+    const unsigned long long kk = *key;
+    for (int step = 0; dist[w] > 1; ++step) {
+        const int dw = dist[w];
+        const unsigned long long t = dev::below(dev::stream_at(kk, (uint64_t)step), sigma[w]);
+        const int end = rp[w + 1];
+        unsigned long long run = 0;
+        int z = -1;
+        for (int base = rp[w]; base < end && z < 0; base += 32) {
+            const int j = base + lane;
+            int c = -1;
+            unsigned long long x = 0;
+            if (j < end) {
+                c = col[j];
+                if (dist[c] == dw - 1) x = sigma[c];
+            }
+            unsigned long long incl = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, x != 0 && run + incl > t);
+            if (m) z = __shfl_sync(0xffffffffu, c, __ffs(m) - 1);
+            else run += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (z < 0) return;  // only with a wrapped path count (reported as an overflow)
+        if (lane == 0) count[z] += 1;
+        w = z;
+    }
+}
+
 // closeness from a forward sweep: every reached vertex other than the source adds its
 // distance and one to its sums
 __global__ void k_add_distances(const int32_t *dist, int32_t n, unsigned long long *far,
@@ -502,7 +544,7 @@ int run(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores, const Ru
         NK_CUDA(cudaEventCreate(&e1));
         NK_CUDA(cudaEventRecord(e0, s));
     }
-    if (cfg.far) a.forward_only = 1;
+    if (cfg.far || cfg.rk_t) a.forward_only = 1;
     for (int32_t i = 0; i < k; ++i) {
         a.src = d_src + i;
         void *args[] = {&a};
@@ -510,6 +552,10 @@ int run(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores, const Ru
         if (cfg.grid_ctas > 0) grid = std::min(grid, cfg.grid_ctas);
         NK_CUDA(cudaLaunchCooperativeKernel(L.fn, dim3(grid), dim3(kThreads), args, 0, s));
         ::nk::count_launch();
+        if (cfg.rk_t) {
+            k_rk_walk<<<1, 32, 0, s>>>(a.rp, a.col, a.dist, a.sp, cfg.rk_t + i, cfg.rk_key + i, cfg.rk_count);
+            ::nk::count_launch();
+        }
         if (cfg.far) {
             k_add_distances<<<std::max(1, std::min((n + 255) / 256, 8 * num_sms())), 256, 0, s>>>(a.dist, n, cfg.far, cfg.reach);
             ::nk::count_launch();

@@ -93,6 +93,8 @@ SIGNATURES = {
     "nk_betweenness_sampled": (_INT, [_P, _U64, _I32, _P]),
     "nk_betweenness_sampled_opts": (_INT, [_P, _U64, _I32, _P, _P]),
     "nk_betweenness_sources": (_INT, [_P, _P, _I32, _D, _P, _P]),
+    "nk_betweenness_rk": (_INT, [_P, ctypes.c_double, ctypes.c_double, _U64, _P, _P, _P, _P]),
+    "nk_vertex_diameter_estimate": (_INT, [_P, _P]),
     "nk_edge_betweenness_exact": (_INT, [_P, _P]),
     "nk_edge_betweenness_sampled": (_INT, [_P, _U64, _I32, _P, _P]),
     "nk_closeness_exact": (_INT, [_P, _P, _P]),
@@ -326,6 +328,23 @@ def betweenness_sources(g: Graph, src, scale: float, opts: RunOpts | None = None
     _check(lib().nk_betweenness_sources(g.handle, sp, k, scale, ptr,
                                          ctypes.byref(o) if o is not None else None))
     return res
+
+
+def vertex_diameter_estimate(g: Graph) -> int:
+    vd = ctypes.c_int32()
+    _check(lib().nk_vertex_diameter_estimate(g.handle, ctypes.byref(vd)))
+    return vd.value
+
+
+def betweenness_rk(g: Graph, epsilon: float, delta: float, seed: int, opts: RunOpts | None = None,
+                   out=None):
+    """(scores, r, vd): the error-bounded estimate after Riondato and Kornaropoulos, on the
+    scale of the exact unordered scores."""
+    ptr, o, res = _out_scores(g, out, opts)
+    r, vd = ctypes.c_int64(), ctypes.c_int32()
+    _check(lib().nk_betweenness_rk(g.handle, epsilon, delta, seed, ptr, ctypes.byref(r), ctypes.byref(vd),
+                                   ctypes.byref(o) if o is not None else None))
+    return res, r.value, vd.value
 
 
 def _arc_count(g: Graph) -> int:

@@ -388,3 +388,71 @@ def test_edge_betweenness_device_output(nk):
     out = torch.full((len(col),), -1.0, dtype=torch.float64, device="cuda")
     nk.edge_betweenness_sampled(g, 2, 256, nk.run_opts(mode=2, batch=256), out=out)
     assert close(out.cpu().numpy(), want)
+
+
+# ------------------------------------------------------------------ error-bounded estimate (Section 3.2)
+RK_MODES = [dict(), dict(mode=1), dict(mode=1, direction=2), dict(mode=2, batch=64, direction=1),
+            dict(mode=2, batch=128, direction=2), dict(mode=2, batch=256)]
+
+
+@pytest.mark.parametrize("name", ["path", "grid", "tree", "components", "isolated", "complete",
+                                  "hubs", "star_big", "hub_path"])
+def test_rk_small_graphs(nk, name):
+    g, rp, col = both(nk, SMALL[name])
+    assert nk.vertex_diameter_estimate(g) == oracle.vertex_diameter_estimate(rp, col)
+    want, r0, vd0 = oracle.betweenness_rk(rp, col, 0.1, 0.1, 7)
+    for m in RK_MODES:
+        got, r, vd = nk.betweenness_rk(g, 0.1, 0.1, 7, nk.run_opts(**m))
+        assert (r, vd) == (r0, vd0)
+        assert np.array_equal(got, want), (name, m)
+
+
+def test_rk_generated(nk):
+    for kind, size, params, eps in (("rmat", 13, {}, 0.05), ("ba", 20000, dict(m0=4), 0.08),
+                                    ("er", 2000, dict(avg_deg=8.0), 0.05)):
+        g = nk.graph_generate(kind, size, 9, **params)
+        n, rp, col = oracle.generate(kind, size, 9, **params)
+        want, r0, vd0 = oracle.betweenness_rk(rp, col, eps, 0.1, 21)
+        for m in (dict(), dict(mode=2, batch=128), dict(mode=1)):
+            got, r, vd = nk.betweenness_rk(g, eps, 0.1, 21, nk.run_opts(**m))
+            assert (r, vd) == (r0, vd0) and np.array_equal(got, want), (kind, m)
+
+
+def test_rk_deep_overflow_and_errors(nk):
+    gp, rp, col = both(nk, G.path(3000))   # deeper than the level slabs: per-source fallback
+    want, r0, _ = oracle.betweenness_rk(rp, col, 0.3, 0.1, 5)
+    got, r, vd = nk.betweenness_rk(gp, 0.3, 0.1, 5, nk.run_opts(mode=2, batch=64))
+    assert r == r0 and vd == 3000 and np.array_equal(got, want)
+    g2, rp2, col2 = both(nk, G.grid(35, 35))
+    seeds = []                                     # the oracle says which seeds overflow
+    for sd in range(12):
+        try:
+            oracle.betweenness_rk(rp2, col2, 0.1, 0.1, sd)
+            seeds.append((sd, False))
+        except oracle.OracleError as eo:
+            assert eo.rc == oracle.ERR_OVERFLOW    # a sampled source near a corner
+            seeds.append((sd, True))
+    assert any(o for _, o in seeds) and not all(o for _, o in seeds)
+    for sd, overflows in seeds[:6]:
+        for opts in (nk.run_opts(mode=1), nk.run_opts(mode=2, batch=64)):
+            if overflows:
+                with pytest.raises(nk.NkError) as e:
+                    nk.betweenness_rk(g2, 0.1, 0.1, sd, opts)
+                assert e.value.rc == nk.ERR_OVERFLOW
+            else:
+                got, _, _ = nk.betweenness_rk(g2, 0.1, 0.1, sd, opts)
+                assert np.array_equal(got, oracle.betweenness_rk(rp2, col2, 0.1, 0.1, sd)[0])
+    for eps, delta in ((0.0, 0.1), (1.0, 0.1), (0.1, 0.0), (0.1, 1.5)):
+        with pytest.raises(nk.NkError) as e:
+            nk.betweenness_rk(gp, eps, delta, 1)
+        assert e.value.rc == nk.ERR_ARG
+
+
+def test_rk_device_output(nk):
+    import torch
+    g = nk.graph_generate("rmat", 12, 3)
+    n, rp, col = oracle.generate("rmat", 12, 3)
+    want, r0, _ = oracle.betweenness_rk(rp, col, 0.07, 0.05, 4)
+    out = torch.full((n,), -1.0, dtype=torch.float64, device="cuda")
+    _, r, _ = nk.betweenness_rk(g, 0.07, 0.05, 4, nk.run_opts(mode=2, batch=256), out=out)
+    assert r == r0 and np.array_equal(out.cpu().numpy(), want)
