@@ -7,7 +7,7 @@ this package, and this package never imports the product library.
 Every function mirrors one C function and cites the passage of the paper it follows:
 Brandes' algorithm, the sampled estimate and the error-bounded estimate after Riondato
 and Kornaropoulos (Section 3.2, Table 1), BFS for unweighted
-graphs (Section 3.4), edge betweenness (Section 4.3), closeness exact and sampled (Table 1),
+graphs and Dijkstra for weighted ones (Section 3.4), edge betweenness (Section 4.3), closeness exact and sampled (Table 1),
 the generators of Section 5 (Table 2).
 """
 from __future__ import annotations
@@ -71,6 +71,9 @@ def _load():
             "or_closeness": (ctypes.c_int, [i32, P, P, i32, P, dbl, P, P]),
             "or_edge_betweenness": (ctypes.c_int, [i32, P, P, i32, P, dbl, P]),
             "or_vertex_diameter_estimate": (ctypes.c_int, [i32, P, P, P]),
+            "or_edge_weights": (ctypes.c_int, [i32, P, P, u64, i32, P]),
+            "or_sssp_weighted": (ctypes.c_int, [i32, P, P, P, i32, P, P]),
+            "or_betweenness_weighted": (ctypes.c_int, [i32, P, P, P, i32, P, dbl, P]),
             "or_rk_sample_count": (i64, [dbl, dbl, i32]),
             "or_rk_path": (i32, [i32, P, P, u64, i64, P, P]),
             "or_betweenness_rk": (ctypes.c_int, [i32, P, P, dbl, dbl, u64, P, P, P]),
@@ -291,6 +294,49 @@ def betweenness_rk(rp, col, eps: float, delta: float, seed: int):
     if rc:
         raise OracleError(rc, "betweenness_rk")
     return out, r.value, vd.value
+
+
+# ---------------------------------------------------------------- weighted graphs (Sections 2.3, 3.4)
+def edge_weights(rp, col, seed: int, wmax: int) -> np.ndarray:
+    """Per arc: the edge {u, v} (u < v) weighs 1 + below(stream(seed, u 2^32 + v), wmax)."""
+    rp, col = _i32(rp), _i32(col)
+    w = np.empty(max(len(col), 1), np.int32)
+    rc = _load().or_edge_weights(len(rp) - 1, _p(rp), _p(col), seed, wmax, _p(w))
+    if rc:
+        raise OracleError(rc, "edge_weights")
+    return w[:len(col)]
+
+
+def sssp_weighted(rp, col, w, s: int):
+    """(dist int64[n] (-1 unreachable), sigma uint64[n]) by Dijkstra from s."""
+    rp, col, w = _i32(rp), _i32(col), _i32(w)
+    n = len(rp) - 1
+    dist = np.empty(n, np.int64)
+    sigma = np.empty(n, np.uint64)
+    rc = _load().or_sssp_weighted(n, _p(rp), _p(col), _p(w), s, _p(dist), _p(sigma))
+    if rc:
+        raise OracleError(rc, "sssp_weighted")
+    return dist, sigma
+
+
+def betweenness_weighted_sources(rp, col, w, src, scale: float) -> np.ndarray:
+    rp, col, w, src = _i32(rp), _i32(col), _i32(w), _i32(src)
+    n = len(rp) - 1
+    out = np.empty(n, np.float64)
+    rc = _load().or_betweenness_weighted(n, _p(rp), _p(col), _p(w), len(src), _p(src), scale, _p(out))
+    if rc:
+        raise OracleError(rc, "betweenness_weighted")
+    return out
+
+
+def betweenness_weighted_exact(rp, col, w) -> np.ndarray:
+    n = len(rp) - 1
+    return betweenness_weighted_sources(rp, col, w, np.arange(n, dtype=np.int32), 0.5)
+
+
+def betweenness_weighted_sampled(rp, col, w, seed: int, k: int) -> np.ndarray:
+    n = len(rp) - 1
+    return betweenness_weighted_sources(rp, col, w, sample_sources(n, seed, k), n / (2.0 * k))
 
 
 # ---------------------------------------------------------------- closeness (Table 1)

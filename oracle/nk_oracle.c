@@ -684,6 +684,151 @@ int or_betweenness_rk(int32_t n, const int32_t *row_ptr, const int32_t *col, dou
 }
 
 /* ------------------------------------------------------------------------------ */
+/* Weighted betweenness (Section 3.4: shortest paths by Dijkstra's algorithm when the */
+/* graph is weighted; Section 2.3: graphs are optionally weighted).  Positive       */
+/* integer weights w[j] per arc, equal on both arcs of an edge, so that path lengths */
+/* are exact and equal-length paths tie exactly.  Per source: Dijkstra with a binary */
+/* heap; sigma[x] += sigma[v] for every arc (v, x) with dist[v] + w = dist[x], taken  */
+/* when v is settled (all of x's predecessors settle before x since w >= 1); then    */
+/* Brandes' accumulation over the settle order reversed.                            */
+/* Random weights: the edge {u, v} (u < v) weighs 1 + below(stream(seed, u 2^32 + v),*/
+/* wmax), the same on both arcs.                                                    */
+/* ------------------------------------------------------------------------------ */
+
+int or_edge_weights(int32_t n, const int32_t *row_ptr, const int32_t *col, uint64_t seed,
+                    int32_t wmax, int32_t *w)
+{
+    if (n < 1 || wmax < 1) return OR_ERR_ARG;
+    for (int32_t u = 0; u < n; ++u)
+        for (int32_t j = row_ptr[u]; j < row_ptr[u + 1]; ++j) {
+            uint64_t a = (uint64_t)(u < col[j] ? u : col[j]), b = (uint64_t)(u < col[j] ? col[j] : u);
+            w[j] = 1 + (int32_t)or_below(or_stream(seed, (a << 32) | b), (uint64_t)wmax);
+        }
+    return OR_OK;
+}
+
+typedef struct { int64_t d; int32_t v; } or_item;
+
+static void or_heap_push(or_item *h, int64_t *len, or_item x)
+{
+    int64_t i = (*len)++;
+    while (i > 0) {
+        int64_t p = (i - 1) / 2;
+        if (h[p].d <= x.d) break;
+        h[i] = h[p];
+        i = p;
+    }
+    h[i] = x;
+}
+
+static or_item or_heap_pop(or_item *h, int64_t *len)
+{
+    or_item top = h[0], x = h[--(*len)];
+    int64_t i = 0;
+    for (;;) {
+        int64_t c = 2 * i + 1;
+        if (c >= *len) break;
+        if (c + 1 < *len && h[c + 1].d < h[c].d) ++c;
+        if (x.d <= h[c].d) break;
+        h[i] = h[c];
+        i = c;
+    }
+    if (*len > 0) h[i] = x;
+    return top;
+}
+
+/* Dijkstra from s: dist (int64, -1 if unreachable), sigma, settle order S (returns its length) */
+static int or_dijkstra(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *w,
+                       int32_t s, int64_t *dist, uint64_t *sigma, int32_t *S, int32_t *ns,
+                       or_item *heap, char *done)
+{
+    int rc = OR_OK;
+    for (int32_t v = 0; v < n; ++v) { dist[v] = -1; sigma[v] = 0; done[v] = 0; }
+    int64_t hl = 0;
+    dist[s] = 0;
+    sigma[s] = 1;
+    or_item first = {0, s};
+    or_heap_push(heap, &hl, first);
+    int32_t cnt = 0;
+    while (hl > 0) {
+        or_item it = or_heap_pop(heap, &hl);
+        int32_t v = it.v;
+        if (done[v] || it.d != dist[v]) continue;
+        done[v] = 1;
+        S[cnt++] = v;
+        for (int32_t j = row_ptr[v]; j < row_ptr[v + 1]; ++j) {
+            int32_t x = col[j];
+            int64_t nd = dist[v] + (int64_t)w[j];
+            if (dist[x] < 0 || nd < dist[x]) {
+                dist[x] = nd;
+                sigma[x] = sigma[v];
+                or_item y = {nd, x};
+                or_heap_push(heap, &hl, y);
+            } else if (nd == dist[x]) {
+                if (__builtin_add_overflow(sigma[x], sigma[v], &sigma[x])) rc = OR_ERR_OVERFLOW;
+            }
+        }
+    }
+    *ns = cnt;
+    return rc;
+}
+
+int or_sssp_weighted(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *w,
+                     int32_t s, int64_t *dist, uint64_t *sigma)
+{
+    if (n < 1 || s < 0 || s >= n) return OR_ERR_ARG;
+    const int64_t A = row_ptr[n];
+    int32_t *S = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    or_item *heap = (or_item *)malloc(sizeof(or_item) * (size_t)(A + 1));
+    char *done = (char *)malloc((size_t)n);
+    int rc = OR_ERR_NOMEM;
+    int32_t ns = 0;
+    if (S && heap && done) rc = or_dijkstra(n, row_ptr, col, w, s, dist, sigma, S, &ns, heap, done);
+    free(S); free(heap); free(done);
+    return rc;
+}
+
+/* scores[v] = scale * sum_{s in src, s != v} delta_s(v) with weighted shortest paths. */
+int or_betweenness_weighted(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *w,
+                            int32_t k, const int32_t *src, double scale, double *scores)
+{
+    if (n < 1 || k < 0) return OR_ERR_ARG;
+    for (int32_t i = 0; i < k; ++i)
+        if (src[i] < 0 || src[i] >= n) return OR_ERR_ARG;
+    const int64_t A = row_ptr[n];
+    for (int64_t j = 0; j < A; ++j)
+        if (w[j] < 1) return OR_ERR_ARG;
+    int64_t *dist = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    uint64_t *sigma = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
+    double *delta = (double *)malloc(sizeof(double) * (size_t)n);
+    int32_t *S = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    or_item *heap = (or_item *)malloc(sizeof(or_item) * (size_t)(A + 1));
+    char *done = (char *)malloc((size_t)n);
+    int rc = (dist && sigma && delta && S && heap && done) ? OR_OK : OR_ERR_NOMEM;
+    for (int32_t v = 0; v < n; ++v) scores[v] = 0.0;
+    for (int32_t i = 0; rc == OR_OK && i < k; ++i) {
+        const int32_t s = src[i];
+        int32_t ns = 0;
+        rc = or_dijkstra(n, row_ptr, col, w, s, dist, sigma, S, &ns, heap, done);
+        if (rc != OR_OK) break;
+        for (int32_t v = 0; v < n; ++v) delta[v] = 0.0;
+        for (int32_t t = ns - 1; t >= 0; --t) {
+            const int32_t x = S[t];
+            for (int32_t j = row_ptr[x]; j < row_ptr[x + 1]; ++j) {
+                const int32_t v = col[j];  /* v precedes x if dist[v] + w = dist[x] */
+                if (dist[v] >= 0 && dist[v] + (int64_t)w[j] == dist[x])
+                    delta[v] += ((double)sigma[v] / (double)sigma[x]) * (1.0 + delta[x]);
+            }
+            if (x != s) scores[x] += delta[x];
+        }
+    }
+    if (rc == OR_OK)
+        for (int32_t v = 0; v < n; ++v) scores[v] *= scale;
+    free(dist); free(sigma); free(delta); free(S); free(heap); free(done);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------------ */
 /* Closeness (Table 1: "closeness", shortest-path search from each node, and its    */
 /* approximation after Eppstein and Wang with s sampled sources).  For every vertex */
 /* v:  far[v] = scale * sum of d(s, v) over the sources s != v that reach v,        */

@@ -121,3 +121,42 @@ def edge_betweenness_bruteforce(n, u, v):
             for x, y in zip(p[:-1], p[1:]):
                 c[(min(x, y), max(x, y))] += Fraction(1, len(ps))
     return c
+
+
+def weighted_bruteforce(rp, col, w):
+    """(dist, sigma, c): by enumerating every simple path of a small weighted graph (no
+    Dijkstra): dist[s][t] = least total weight (-1 unreachable), sigma[s][t] = number of
+    simple paths of that weight, c[v] = exact rational betweenness (unordered pairs)."""
+    rp, col, w = list(map(int, rp)), list(map(int, col)), list(map(int, w))
+    n = len(rp) - 1
+    best = [[None] * n for _ in range(n)]
+    paths = [[[] for _ in range(n)] for _ in range(n)]
+
+    def dfs(s, v, seen, path, length):
+        if best[s][v] is None or length < best[s][v]:
+            best[s][v] = length
+            paths[s][v] = [tuple(path)]
+        elif length == best[s][v]:
+            paths[s][v].append(tuple(path))
+        for j in range(rp[v], rp[v + 1]):
+            x = col[j]
+            if x not in seen:
+                seen.add(x)
+                path.append(x)
+                dfs(s, x, seen, path, length + w[j])
+                path.pop()
+                seen.remove(x)
+
+    for s in range(n):
+        dfs(s, s, {s}, [s], 0)
+    dist = [[-1 if best[s][t] is None else best[s][t] for t in range(n)] for s in range(n)]
+    sigma = [[len(paths[s][t]) for t in range(n)] for s in range(n)]
+    c = [Fraction(0)] * n
+    for s, t in itertools.combinations(range(n), 2):
+        ps = paths[s][t]
+        if not ps:
+            continue
+        for p in ps:
+            for x in p[1:-1]:
+                c[x] += Fraction(1, len(ps))
+    return dist, sigma, c

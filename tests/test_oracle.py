@@ -703,3 +703,81 @@ def test_rk_small_vertex_diameter_gives_zero():
     _, rp, col = csr(G.complete(6))
     sc, r, vd = oracle.betweenness_rk(rp, col, 0.2, 0.2, 1)
     assert vd == 3 and r == oracle.rk_sample_count(0.2, 0.2, 3) and np.all(sc == 0)
+
+
+# ------------------------------------------------------------------ weighted graphs (Sections 2.3, 3.4)
+def test_edge_weights_symmetric_and_in_range():
+    n, rp, col = oracle.generate("er", 300, 2, avg_deg=6.0)
+    w = oracle.edge_weights(rp, col, 9, 7)
+    assert w.min() >= 1 and w.max() <= 7 and len(set(w.tolist())) == 7
+    for u in range(0, n, 7):
+        for j in range(rp[u], rp[u + 1]):
+            v = col[j]
+            r = rp[v] + int(np.searchsorted(col[rp[v]:rp[v + 1]], u))
+            assert w[r] == w[j]
+    assert np.all(oracle.edge_weights(rp, col, 9, 1) == 1)
+
+
+@pytest.mark.parametrize("graph", [G.grid(6, 7), G.gnp(150, 0.04, 2), G.hypercube(5),
+                                   G.disjoint_union(G.cycle(12), G.star(6), G.complete(1))])
+def test_weighted_reduces_to_unweighted(graph):
+    n, rp, col = csr(graph)
+    base = oracle.betweenness_exact(rp, col)
+    for c in (1, 3):
+        w = np.full(len(col), c, np.int32)
+        assert np.allclose(oracle.betweenness_weighted_exact(rp, col, w), base, rtol=1e-12, atol=1e-12)
+        for s in (0, n // 2):
+            d, sg = oracle.sssp_weighted(rp, col, w, s)
+            d0, s0 = oracle.bfs(rp, col, s)
+            assert np.array_equal(d, np.where(d0 >= 0, c * d0.astype(np.int64), -1))
+            assert np.array_equal(sg, s0)
+
+
+def test_weighted_trees_and_paths_ignore_weights():
+    for g in (G.path(20), G.random_tree(120, 6)):
+        n, rp, col = csr(g)
+        w = oracle.edge_weights(rp, col, 4, 9)
+        assert np.allclose(oracle.betweenness_weighted_exact(rp, col, w), oracle.betweenness_exact(rp, col),
+                           rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_weighted_bruteforce_small(seed):
+    from bruteforce import weighted_bruteforce
+    rng = np.random.default_rng(300 + seed)
+    n = int(rng.integers(5, 9))
+    g = G.gnp(n, float(rng.uniform(0.3, 0.7)), seed) if seed % 3 else G.disjoint_union(G.cycle(4), G.gnp(n - 4, 0.6, seed))
+    n, rp, col = csr(g)
+    w = oracle.edge_weights(rp, col, seed, 1 + seed % 4)   # wmax 1..4: many equal-length ties
+    dist, sigma, c = weighted_bruteforce(rp, col, w)
+    for s in range(n):
+        d, sg = oracle.sssp_weighted(rp, col, w, s)
+        assert d.tolist() == dist[s]
+        assert sg.tolist() == [sigma[s][t] if dist[s][t] >= 0 else 0 for t in range(n)]
+    got = oracle.betweenness_weighted_exact(rp, col, w)
+    assert np.allclose(got, [float(x) for x in c], rtol=1e-12, atol=1e-12)
+
+
+def test_weighted_cycle_with_a_heavy_edge():
+    # C_4 = 0-1-2-3-0 with w(3,0) = 3: 0 reaches 3 by 0-1-2-3 (length 3) and by the edge
+    # (length 3), so the pair {0, 3} splits over two paths; every other pair has one path
+    n, u, v = G.cycle(4)
+    rp, col = oracle.csr_build(n, u, v)
+    w = np.ones(len(col), np.int32)
+    for j in range(len(col)):
+        a = int(np.searchsorted(rp, j, side="right") - 1)
+        if {a, int(col[j])} == {0, 3}:
+            w[j] = 3
+    d, sg = oracle.sssp_weighted(rp, col, w, 0)
+    assert d.tolist() == [0, 1, 2, 3] and sg.tolist() == [1, 1, 1, 2]
+    c = oracle.betweenness_weighted_exact(rp, col, w)
+    # vertex 1: {0,2} (1 path, via 1) + {0,3} (1 of 2) = 1.5; vertex 2: {1,3} + {0,3}/2 = 1.5;
+    # vertex 0: {1,3}? 1-0-3 weighs 4 > 1-2-3: 0; vertex 3: {0,2}? 0-3-2 weighs 4: 0
+    assert np.allclose(c, [0.0, 1.5, 1.5, 0.0], rtol=1e-14)
+
+
+def test_weighted_sampled_k_equals_n():
+    n, rp, col = oracle.generate("ba", 400, 3, m0=3)
+    w = oracle.edge_weights(rp, col, 5, 10)
+    assert np.array_equal(oracle.betweenness_weighted_sampled(rp, col, w, 8, n),
+                          oracle.betweenness_weighted_exact(rp, col, w))
