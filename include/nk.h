@@ -194,6 +194,30 @@ int nk_last_run_stats(nk_run_stats *out);
  * calls with batch/alpha = 0 use it). */
 int nk_autotune(const nk_graph *g, uint64_t seed, int32_t k, nk_run_opts *best);
 
+/* ---------------------------------------------------------------- weighted graphs (Sections 2.3, 3.4) */
+/* Graphs are optionally weighted (Section 2.3); shortest paths then come from Dijkstra's
+ * algorithm instead of BFS (Section 3.4).  Weights are positive integers, one per arc of the
+ * canonical CSR (A entries, in the order of nk_graph_export_csr), equal on both arcs of an
+ * edge, so path lengths are exact and equal-length paths tie exactly.
+ * nk_graph_set_weights copies w (device pointer with NK_CSR_DEVICE_PTRS, else host) and
+ * checks it: NK_ERR_GRAPH if a weight is < 1 or the two arcs of an edge differ.
+ * nk_graph_random_weights gives the edge {u, v}, u < v, the weight
+ * 1 + floor(x * wmax / 2^64) with x the (u 2^32 + v)-th output of the SplitMix64 stream
+ * seeded with seed (wmax >= 1).  nk_graph_export_weights copies them to host memory.
+ * nk_sssp_weighted: dist (int64, -1 if unreachable) and sigma (uint64, NK_ERR_OVERFLOW above
+ * 2^64 - 1) from source s, host buffers of n entries.
+ * nk_betweenness_weighted_exact / _sampled: as nk_betweenness_exact / _sampled (unordered
+ * pairs, scale 1/2 or n/(2k), the same sampler) with weighted shortest paths; NK_ERR_ARG if
+ * the graph has no weights.  The search settles the vertices in buckets of equal distance,
+ * one persistent launch per source. */
+int nk_graph_set_weights(nk_graph *g, const int32_t *w, uint32_t flags);
+int nk_graph_random_weights(nk_graph *g, uint64_t seed, int32_t wmax);
+int nk_graph_export_weights(const nk_graph *g, int32_t *w);
+int nk_sssp_weighted(const nk_graph *g, int32_t s, int64_t *dist, uint64_t *sigma);
+int nk_betweenness_weighted_exact(const nk_graph *g, double *scores);
+int nk_betweenness_weighted_sampled(const nk_graph *g, uint64_t seed, int32_t k, double *scores,
+                                    const nk_run_opts *opts);
+
 /* ---------------------------------------------------------------- error-bounded estimate (Section 3.2) */
 /* Betweenness with an error bound, after Riondato and Kornaropoulos (cited in Section 3.2 as
  * the estimate whose scores are within +-epsilon of the exact ones with a user-chosen

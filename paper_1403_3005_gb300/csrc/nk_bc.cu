@@ -481,6 +481,44 @@ int rk_entry(const nk_graph *gc, double eps, double delta, uint64_t seed, double
     return NK_OK;
 }
 
+// Weighted betweenness entry (Dijkstra sweeps): all vertices (scale 1/2) or k sampled
+// sources (scale n/(2k)).
+int weighted_entry(const nk_graph *gc, bool sample, uint64_t seed, int32_t k, double *scores,
+                   const nk_run_opts *opts)
+{
+    if (!gc) return set_error(NK_ERR_ARG, "graph is null");
+    if (!scores) return set_error(NK_ERR_ARG, "scores is null");
+    nk_graph *g = const_cast<nk_graph *>(gc);
+    const int32_t n = g->n;
+    if (sample && (k < 1 || k > n)) return set_error(NK_ERR_ARG, "need 1 <= k <= n (k=%d, n=%d)", k, n);
+    if (!sample) k = n;
+    RunCfg cfg = cfg_of(opts, g);
+    NK_TRY(check_cfg(cfg));
+    const bool dev = opts && (opts->flags & NK_RUN_DEVICE_PTRS);
+    cudaStream_t s = stream();
+    std::lock_guard<std::mutex> lock(g->mu);
+    Tmp dsrc, dsc;
+    NK_TRY(dsrc.alloc(sizeof(int32_t) * k, s));
+    if (sample) {
+        NK_TRY(sample_sources_device(n, seed, k, dsrc.as<int32_t>(), s));
+    } else {
+        k_iota<<<std::max(1, std::min((k + 255) / 256, 8 * num_sms())), 256, 0, s>>>(dsrc.as<int32_t>(), k);
+        ::nk::count_launch();
+    }
+    double *d_scores = scores;
+    if (!dev) {
+        NK_TRY(dsc.alloc(sizeof(double) * (size_t)n, s));
+        d_scores = dsc.as<double>();
+    }
+    NK_CUDA(cudaMemsetAsync(d_scores, 0, sizeof(double) * (size_t)n, s));
+    t_stats = RunStats();
+    NK_TRY(run_weighted(g, dsrc.as<int32_t>(), k, d_scores, cfg, &t_stats, s, nullptr, nullptr));
+    NK_TRY(scale_vector(d_scores, n, sample ? (double)n / (2.0 * (double)k) : 0.5, s));
+    if (!dev) NK_CUDA(cudaMemcpyAsync(scores, d_scores, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, s));
+    NK_CUDA(cudaStreamSynchronize(s));
+    return NK_OK;
+}
+
 }  // namespace
 }  // namespace nk
 
@@ -512,6 +550,68 @@ int nk_betweenness_sources(const nk_graph *g, const int32_t *src, int32_t k, dou
 {
     if (!src) return set_error(NK_ERR_ARG, "src is null");
     return bc_entry(g, src, k, false, 0, scale, scores, opts);
+}
+
+int nk_graph_set_weights(nk_graph *g, const int32_t *w, uint32_t flags)
+{
+    if (!g || !w) return set_error(NK_ERR_ARG, "graph or weights is null");
+    cudaStream_t s = stream();
+    std::lock_guard<std::mutex> lock(g->mu);
+    if (flags & NK_CSR_DEVICE_PTRS) return set_weights_device(g, w, s);
+    Tmp dw;
+    NK_TRY(dw.alloc(sizeof(int32_t) * (size_t)std::max<int64_t>(g->A, 1), s));
+    if (g->A > 0) NK_CUDA(cudaMemcpyAsync(dw.p, w, sizeof(int32_t) * (size_t)g->A, cudaMemcpyHostToDevice, s));
+    return set_weights_device(g, dw.as<int32_t>(), s);
+}
+
+int nk_graph_random_weights(nk_graph *g, uint64_t seed, int32_t wmax)
+{
+    if (!g) return set_error(NK_ERR_ARG, "graph is null");
+    std::lock_guard<std::mutex> lock(g->mu);
+    return random_weights(g, seed, wmax, stream());
+}
+
+int nk_graph_export_weights(const nk_graph *g, int32_t *w)
+{
+    if (!g || !w) return set_error(NK_ERR_ARG, "graph or output is null");
+    if (!g->weighted) return set_error(NK_ERR_ARG, "the graph has no weights");
+    cudaStream_t s = stream();
+    if (g->A > 0) NK_CUDA(cudaMemcpyAsync(w, g->wt.p, sizeof(int32_t) * (size_t)g->A, cudaMemcpyDeviceToHost, s));
+    NK_CUDA(cudaStreamSynchronize(s));
+    return NK_OK;
+}
+
+int nk_sssp_weighted(const nk_graph *gc, int32_t src, int64_t *dist, uint64_t *sigma)
+{
+    if (!gc || !dist || !sigma) return set_error(NK_ERR_ARG, "null argument");
+    if (src < 0 || src >= gc->n) return set_error(NK_ERR_ARG, "source %d outside [0, %d)", src, gc->n);
+    nk_graph *g = const_cast<nk_graph *>(gc);
+    cudaStream_t s = stream();
+    std::lock_guard<std::mutex> lock(g->mu);
+    const int32_t n = g->n;
+    Tmp ds, out;
+    NK_TRY(ds.alloc(sizeof(int32_t), s));
+    NK_TRY(out.alloc(16 * (size_t)n, s));
+    NK_CUDA(cudaMemcpyAsync(ds.p, &src, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    long long *dd = out.as<long long>();
+    uint64_t *dsig = reinterpret_cast<uint64_t *>(dd + n);
+    RunCfg cfg;
+    NK_TRY(run_weighted(g, ds.as<int32_t>(), 1, nullptr, cfg, nullptr, s, dd, dsig));
+    NK_CUDA(cudaMemcpyAsync(dist, dd, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost, s));
+    NK_CUDA(cudaMemcpyAsync(sigma, dsig, sizeof(uint64_t) * (size_t)n, cudaMemcpyDeviceToHost, s));
+    NK_CUDA(cudaStreamSynchronize(s));
+    return NK_OK;
+}
+
+int nk_betweenness_weighted_exact(const nk_graph *g, double *scores)
+{
+    return weighted_entry(g, false, 0, 0, scores, nullptr);
+}
+
+int nk_betweenness_weighted_sampled(const nk_graph *g, uint64_t seed, int32_t k, double *scores,
+                                    const nk_run_opts *opts)
+{
+    return weighted_entry(g, true, seed, k, scores, opts);
 }
 
 int nk_betweenness_rk(const nk_graph *g, double epsilon, double delta, uint64_t seed, double *scores,

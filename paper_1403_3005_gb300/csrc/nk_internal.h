@@ -137,6 +137,8 @@ struct nk_graph {
     std::vector<int32_t> h_hv, h_hfirst;  // host copies of heavy[0] and heavy[1]
     nk::CapturedRun captured;             // last call captured with NK_RUN_CUDA_GRAPH
     int32_t vd_est = -1;                  // cached vertex-diameter bound (nk_rk.cu), -1 = not yet
+    nk::DevBuf wt;                        // int32[A] arc weights (nk_weighted.cu), when weighted
+    bool weighted = false;
 };
 
 namespace nk {
@@ -149,6 +151,12 @@ int64_t rk_sample_count(double eps, double delta, int32_t vd);
 // The r sampled pairs (src -> tgt) and the keys of their path walks.
 int rk_pairs(uint64_t seed, int32_t n, int64_t r, int32_t *src, int32_t *tgt, unsigned long long *key,
              cudaStream_t s);
+
+// ---------------------------------------------------------------- weighted graphs (nk_weighted.cu)
+// Copies device weights into the graph and checks them (>= 1, equal on both arcs).
+int set_weights_device(nk_graph *g, const int32_t *d_w, cudaStream_t s);
+// Symmetric random weights 1 + below(stream(seed, u 2^32 + v), wmax) for the edge {u < v}.
+int random_weights(nk_graph *g, uint64_t seed, int32_t wmax, cudaStream_t s);
 
 // ---------------------------------------------------------------- primitives (nk_core.cu)
 // Exclusive prefix sum of count int64 values (in may equal out); *total (device, may be
@@ -211,6 +219,12 @@ struct RunStats {
 int run_per_source(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores,
                    const RunCfg &cfg, RunStats *st, cudaStream_t s);
 int run_sssp(nk_graph *g, int32_t src, int32_t *d_dist, uint64_t *d_sigma, cudaStream_t s);
+// Dijkstra-based sweeps of k device sources (per-source persistent launches); scores (device,
+// zeroed by the caller, or null for the forward sweep only) += delta.  dist_out (int64, -1
+// for unreachable) and sigma_out (device, optional) receive the last source's search.
+int run_weighted(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores, const RunCfg &cfg,
+                 RunStats *st, cudaStream_t s, long long *dist_out, uint64_t *sigma_out);
+
 
 // Batched multi-source form (nk_batch.cu).  Returns NK_OK, or an error; sources of a
 // batch whose BFS is deeper than the level cap are re-run by the per-source form.

@@ -93,6 +93,12 @@ SIGNATURES = {
     "nk_betweenness_sampled": (_INT, [_P, _U64, _I32, _P]),
     "nk_betweenness_sampled_opts": (_INT, [_P, _U64, _I32, _P, _P]),
     "nk_betweenness_sources": (_INT, [_P, _P, _I32, _D, _P, _P]),
+    "nk_graph_set_weights": (_INT, [_P, _P, _U32]),
+    "nk_graph_random_weights": (_INT, [_P, _U64, _I32]),
+    "nk_graph_export_weights": (_INT, [_P, _P]),
+    "nk_sssp_weighted": (_INT, [_P, _I32, _P, _P]),
+    "nk_betweenness_weighted_exact": (_INT, [_P, _P]),
+    "nk_betweenness_weighted_sampled": (_INT, [_P, _U64, _I32, _P, _P]),
     "nk_betweenness_rk": (_INT, [_P, ctypes.c_double, ctypes.c_double, _U64, _P, _P, _P, _P]),
     "nk_vertex_diameter_estimate": (_INT, [_P, _P]),
     "nk_edge_betweenness_exact": (_INT, [_P, _P]),
@@ -327,6 +333,46 @@ def betweenness_sources(g: Graph, src, scale: float, opts: RunOpts | None = None
         src = s
     _check(lib().nk_betweenness_sources(g.handle, sp, k, scale, ptr,
                                          ctypes.byref(o) if o is not None else None))
+    return res
+
+
+def set_weights(g: Graph, w) -> None:
+    """Arc weights (int32 >= 1, equal on both arcs of an edge): numpy array or CUDA tensor."""
+    if _is_torch(w):
+        _check(lib().nk_graph_set_weights(g.handle, _dev_ptr(w), CSR_DEVICE_PTRS))
+    else:
+        wh = _host_i32(w)
+        _check(lib().nk_graph_set_weights(g.handle, _np_ptr(wh), 0))
+
+
+def random_weights(g: Graph, seed: int, wmax: int) -> None:
+    _check(lib().nk_graph_random_weights(g.handle, seed, wmax))
+
+
+def export_weights(g: Graph) -> np.ndarray:
+    A = _arc_count(g)
+    w = np.empty(max(A, 1), np.int32)
+    _check(lib().nk_graph_export_weights(g.handle, _np_ptr(w)))
+    return w[:A]
+
+
+def sssp_weighted(g: Graph, s: int):
+    dist = np.empty(g.n, np.int64)
+    sigma = np.empty(g.n, np.uint64)
+    _check(lib().nk_sssp_weighted(g.handle, s, _np_ptr(dist), _np_ptr(sigma)))
+    return dist, sigma
+
+
+def betweenness_weighted_exact(g: Graph) -> np.ndarray:
+    out = np.empty(g.n, np.float64)
+    _check(lib().nk_betweenness_weighted_exact(g.handle, _np_ptr(out)))
+    return out
+
+
+def betweenness_weighted_sampled(g: Graph, seed: int, k: int, opts: RunOpts | None = None, out=None):
+    ptr, o, res = _out_scores(g, out, opts)
+    _check(lib().nk_betweenness_weighted_sampled(g.handle, seed, k, ptr,
+                                                 ctypes.byref(o) if o is not None else None))
     return res
 
 

@@ -456,3 +456,62 @@ def test_rk_device_output(nk):
     out = torch.full((n,), -1.0, dtype=torch.float64, device="cuda")
     _, r, _ = nk.betweenness_rk(g, 0.07, 0.05, 4, nk.run_opts(mode=2, batch=256), out=out)
     assert r == r0 and np.array_equal(out.cpu().numpy(), want)
+
+
+# ------------------------------------------------------------------ weighted graphs (Sections 2.3, 3.4)
+def weighted_both(nk, graph, seed, wmax):
+    g, rp, col = both(nk, graph)
+    nk.random_weights(g, seed, wmax)
+    return g, rp, col, oracle.edge_weights(rp, col, seed, wmax)
+
+
+def test_weights_generated_identically_and_checked(nk):
+    g, rp, col, w = weighted_both(nk, G.gnp(300, 0.03, 1), 5, 9)
+    assert np.array_equal(nk.export_weights(g), w)
+    nk.set_weights(g, w)
+    assert np.array_equal(nk.export_weights(g), w)
+    for bad in (w + np.eye(1, len(w), 0, dtype=np.int32)[0], np.zeros_like(w)):
+        with pytest.raises(nk.NkError) as e:
+            nk.set_weights(g, bad)
+        assert e.value.rc == nk.ERR_GRAPH
+    g2, _, _ = both(nk, G.path(10))
+    with pytest.raises(nk.NkError) as e:
+        nk.betweenness_weighted_exact(g2)
+    assert e.value.rc == nk.ERR_ARG
+
+
+@pytest.mark.parametrize("name", ["path", "cycle_even", "k_ab", "grid", "hypercube", "tree", "gnp",
+                                  "components", "isolated", "hubs", "hub_path"])
+def test_weighted_exact_small(nk, name):
+    for wmax in (1, 3, 50):
+        g, rp, col, w = weighted_both(nk, SMALL[name], 7 + wmax, wmax)
+        n = len(rp) - 1
+        assert close(nk.betweenness_weighted_exact(g), oracle.betweenness_weighted_exact(rp, col, w)), wmax
+        for s in sorted({0, n // 3, n - 1}):
+            d, sg = nk.sssp_weighted(g, s)
+            d0, s0 = oracle.sssp_weighted(rp, col, w, s)
+            assert np.array_equal(d, d0) and np.array_equal(sg, s0), (wmax, s)
+
+
+def test_weighted_sampled_generated(nk):
+    for kind, size, params, wmax, k in (("rmat", 12, {}, 16, 100), ("ba", 5000, dict(m0=4), 5, 64),
+                                        ("er", 2000, dict(avg_deg=8.0), 100, 50)):
+        g = nk.graph_generate(kind, size, 4, **params)
+        n, rp, col = oracle.generate(kind, size, 4, **params)
+        nk.random_weights(g, 12, wmax)
+        w = oracle.edge_weights(rp, col, 12, wmax)
+        want = oracle.betweenness_weighted_sampled(rp, col, w, 6, k)
+        assert close(nk.betweenness_weighted_sampled(g, 6, k), want), kind
+
+
+def test_weighted_overflow_and_device_output(nk):
+    import torch
+    g, rp, col, w = weighted_both(nk, G.grid(35, 35), 1, 1)
+    with pytest.raises(nk.NkError) as e:
+        nk.sssp_weighted(g, 0)
+    assert e.value.rc == nk.ERR_OVERFLOW
+    g, rp, col, w = weighted_both(nk, G.gnp(500, 0.02, 3), 2, 20)
+    want = oracle.betweenness_weighted_sampled(rp, col, w, 3, 40)
+    out = torch.full((500,), -1.0, dtype=torch.float64, device="cuda")
+    nk.betweenness_weighted_sampled(g, 3, 40, None, out=out)
+    assert close(out.cpu().numpy(), want)
