@@ -40,10 +40,29 @@ struct WArgs {
     int32_t *bcnt;           // [n + 3] vertices of bucket b
     int32_t *boff;           // [n + 3] start of bucket b in order
     long long *bnext;        // [n + 3] smallest tentative distance noted in iteration b
+    long long *bdist;        // [n + 3] distance of bucket b
     double *scores;          // += delta (null: forward only)
     Ctrl *ctrl;
     uint64_t limit_ns;
+    // rows longer than kHeavyChunk arcs are split into chunks handled by different warps
+    const int32_t *hv, *hfirst, *chunk_h;
+    int32_t H, C;
+    unsigned long long *part;  // [C] per-chunk psi partial sums (double-single)
 };
+
+__device__ __forceinline__ bool heavy(const WArgs &a, int v)
+{
+    return a.H > 0 && __ldg(a.rp + v + 1) - __ldg(a.rp + v) > kHeavyChunk;
+}
+
+// Chunk c of a heavy vertex: its vertex h and arc range [j0, j1).
+__device__ __forceinline__ void chunk_of(const WArgs &a, long long c, int &h, int &j0, int &j1)
+{
+    const int i = __ldg(a.chunk_h + c);
+    h = __ldg(a.hv + i);
+    j0 = __ldg(a.rp + h) + (int)(c - __ldg(a.hfirst + i)) * kHeavyChunk;
+    j1 = min(j0 + kHeavyChunk, __ldg(a.rp + h + 1));
+}
 
 __device__ __forceinline__ long long ld_dist(const long long *p)
 {
@@ -96,16 +115,19 @@ __global__ void __launch_bounds__(kThreads) k_wsource(WArgs a)
         atomicMin(&s_min, mymin);
         __syncthreads();
         if (threadIdx.x == 0 && s_min < kInf) atomicMin(a.bnext + b, s_min);
-        if (tid == 0) a.boff[b] = qtail;
+        if (tid == 0) {
+            a.boff[b] = qtail;
+            a.bdist[b] = D;
+        }
         if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
         const int nb = dev::ldcg(a.bcnt + b);
-        // ---- settle: pull sigma from the predecessors, relax the arcs (warp per vertex)
+        // ---- settle: pull sigma from the predecessors, relax the arcs (warp per light
+        //      vertex; heavy vertices chunk by chunk, their sigma summed with integer
+        //      atomics, which are exact in any order)
         long long lmin = kInf;
-        for (long long i = wid; i < nb; i += nw) {
-            const int v = dev::ldcg(a.order + qtail + i);
-            const int beg = __ldg(a.rp + v), end = __ldg(a.rp + v + 1);
+        auto settle_arcs = [&](int v, int j0, int j1) -> unsigned long long {
             unsigned long long sig = 0;
-            for (int j = beg + lane; j < end; j += 32) {
+            for (int j = j0 + lane; j < j1; j += 32) {
                 const int x = __ldg(a.col + j);
                 const long long wj = __ldg(a.w + j);
                 const long long dx = ld_dist(a.dist + x);
@@ -120,9 +142,22 @@ __global__ void __launch_bounds__(kThreads) k_wsource(WArgs a)
                     lmin = min(lmin, nd);
                 }
             }
-            if (v != s) {
-                sig = dev::group_sum_u64<32>(sig, ovf);
-                if (lane == 0) a.sp[v] = sig;
+            return dev::group_sum_u64<32>(sig, ovf);
+        };
+        for (long long i = wid; i < nb; i += nw) {
+            const int v = dev::ldcg(a.order + qtail + i);
+            if (heavy(a, v)) continue;
+            const unsigned long long sig = settle_arcs(v, __ldg(a.rp + v), __ldg(a.rp + v + 1));
+            if (v != s && lane == 0) a.sp[v] = sig;
+        }
+        for (long long c = wid; c < a.C; c += nw) {
+            int h, j0, j1;
+            chunk_of(a, c, h, j0, j1);
+            if (ld_dist(a.dist + h) != D) continue;
+            const unsigned long long sig = settle_arcs(h, j0, j1);
+            if (h != s && lane == 0 && sig != 0) {
+                const unsigned long long old = atomicAdd(a.sp + h, sig);
+                ovf |= old + sig < old;
             }
         }
         atomicMin(&s_min, lmin);  // s_min still holds the scan minimum of this block
@@ -141,23 +176,46 @@ __global__ void __launch_bounds__(kThreads) k_wsource(WArgs a)
     }
     if (ovf) atomicOr(&a.ctrl->ovf, 1);
     if (!a.scores) return;
-    // ---- backward, last bucket first
+    // ---- backward, last bucket first; heavy vertices sum per-chunk partials in chunk order
+    auto psi_sum = [&](long long dv, int j0, int j1) {
+        dev::ff acc = dev::ff_zero();
+        for (int j = j0 + lane; j < j1; j += 32) {
+            const int x = __ldg(a.col + j);
+            if (ld_dist(a.dist + x) == dv + __ldg(a.w + j)) acc = dev::ff_add(acc, dev::ff_unpack(dev::ldcg(a.sp + x)));
+        }
+        return dev::group_sum_ff<32>(acc);
+    };
+    auto finish = [&](int v, dev::ff acc) {
+        const dev::ff sv = dev::ff_from_u64(dev::ldcg(a.sp + v));
+        const dev::ff delta = dev::ff_mul(sv, acc);
+        a.sp[v] = dev::ff_pack(dev::ff_add(dev::ff_rcp(sv), acc));
+        if (v != s && delta.hi != 0.0f) a.scores[v] += dev::ff_to_double(delta);
+    };
     for (int bb = nbk - 1; bb >= 0; --bb) {
         const int off = dev::ldcg(a.boff + bb), cnt = dev::ldcg(a.bcnt + bb);
+        const long long Db = dev::ldcg(a.bdist + bb);
         for (long long i = wid; i < cnt; i += nw) {
             const int v = dev::ldcg(a.order + off + i);
-            const long long dv = ld_dist(a.dist + v);
-            dev::ff acc = dev::ff_zero();
-            for (int j = __ldg(a.rp + v) + lane; j < __ldg(a.rp + v + 1); j += 32) {
-                const int x = __ldg(a.col + j);
-                if (ld_dist(a.dist + x) == dv + __ldg(a.w + j)) acc = dev::ff_add(acc, dev::ff_unpack(dev::ldcg(a.sp + x)));
+            if (heavy(a, v)) continue;
+            const dev::ff acc = psi_sum(Db, __ldg(a.rp + v), __ldg(a.rp + v + 1));
+            if (lane == 0) finish(v, acc);
+        }
+        if (a.H > 0) {
+            for (long long c = wid; c < a.C; c += nw) {
+                int h, j0, j1;
+                chunk_of(a, c, h, j0, j1);
+                if (ld_dist(a.dist + h) != Db) continue;
+                const dev::ff acc = psi_sum(Db, j0, j1);
+                if (lane == 0) a.part[c] = dev::ff_pack(acc);
             }
-            acc = dev::group_sum_ff<32>(acc);
-            if (lane == 0) {
-                const dev::ff sv = dev::ff_from_u64(dev::ldcg(a.sp + v));
-                const dev::ff delta = dev::ff_mul(sv, acc);
-                a.sp[v] = dev::ff_pack(dev::ff_add(dev::ff_rcp(sv), acc));
-                if (v != s && delta.hi != 0.0f) a.scores[v] += dev::ff_to_double(delta);
+            if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+            for (long long i = tid; i < a.H; i += nthr) {
+                const int h = __ldg(a.hv + i);
+                if (ld_dist(a.dist + h) != Db) continue;
+                dev::ff acc = dev::ff_zero();
+                for (int c = __ldg(a.hfirst + i); c < __ldg(a.hfirst + i + 1); ++c)
+                    acc = dev::ff_add(acc, dev::ff_unpack(dev::ldcg(a.part + c)));
+                finish(h, acc);
             }
         }
         if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
@@ -243,7 +301,9 @@ int run_weighted(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores,
     const int32_t n = g->n;
     const size_t lv = (size_t)n + 3;
     Tmp buf;
-    const size_t bytes = 8 * (size_t)n * 2 + 4 * (size_t)n + 4 * lv * 2 + 8 * lv + sizeof(Ctrl) + 64;
+    NK_TRY(build_heavy(g, s));
+    const size_t C = (size_t)std::max(g->heavy_C, 0);
+    const size_t bytes = 8 * (size_t)n * 2 + 4 * (size_t)n + 4 * lv * 2 + 16 * lv + 8 * (C + 1) + sizeof(Ctrl) + 64;
     NK_TRY(buf.alloc(bytes, s));
     char *p = buf.as<char>();
     WArgs a;
@@ -257,7 +317,15 @@ int run_weighted(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores,
     a.order = reinterpret_cast<int32_t *>(p + 16 * (size_t)n + 8 * lv);
     a.bcnt = a.order + n;
     a.boff = a.bcnt + lv;
-    a.ctrl = reinterpret_cast<Ctrl *>(p + ((16 * (size_t)n + 8 * lv + 4 * (size_t)n + 8 * lv + 15) & ~(size_t)15));
+    const size_t o_bdist = (16 * (size_t)n + 8 * lv + 4 * (size_t)n + 8 * lv + 7) & ~(size_t)7;
+    a.bdist = reinterpret_cast<long long *>(p + o_bdist);
+    a.part = reinterpret_cast<unsigned long long *>(p + o_bdist + 8 * lv);
+    a.ctrl = reinterpret_cast<Ctrl *>(p + ((o_bdist + 8 * lv + 8 * (C + 1) + 15) & ~(size_t)15));
+    a.hv = g->heavy[0].as<int32_t>();
+    a.hfirst = g->heavy[1].as<int32_t>();
+    a.chunk_h = g->heavy[2].as<int32_t>();
+    a.H = std::max(g->heavy_H, 0);
+    a.C = (int32_t)C;
     a.scores = d_scores;
     a.limit_ns = cfg.limit_ns ? cfg.limit_ns : wait_limit_ns();
     static int bps = -1;
