@@ -62,6 +62,7 @@ def parse():
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-per-source", action="store_true")
+    p.add_argument("--no-ext", action="store_true", help="skip the closeness / edge / estimate / weighted legs")
     p.add_argument("--batch", type=int, default=0)
     return p.parse_args()
 
@@ -282,6 +283,169 @@ def cpu_baseline(cfg, seconds, rank_seed):
                       f"oracle-generated graph, {t:.1f} s on 1 host core"}
 
 
+# ------------------------------------------------------------------ widened rows
+def closeness_bytes(n, A, B, depth):
+    """Closeness, per batched launch: the forward half of the betweenness model,
+    (4A + 12n) + 17nB, plus the level-sum pass (depth slabs of 8nB/64 bytes read, the two
+    uint64 sums read and written, 32n)."""
+    return (4.0 * A + 12.0 * n) + 17.0 * n * B + 8.0 * n * (B // 64) * depth + 32.0 * n
+
+
+def edge_bytes(n, A, B):
+    """Edge betweenness, per batched launch: the betweenness model plus the per-arc sums read
+    and written once (16A)."""
+    return algorithmic_bytes_per_launch(n, A, B) + 16.0 * A
+
+
+def rk_bytes(n, A, B):
+    """Error-bounded estimate, per batched launch: the forward half of the betweenness model
+    (the path walks read a few rows per sample)."""
+    return (4.0 * A + 12.0 * n) + 17.0 * n * B
+
+
+def weighted_bytes(n, A):
+    """Weighted betweenness, per source: column ids and weights read in each sweep (16A), row
+    offsets twice (8n), distance, sigma/psi written and read (32n), the score read and
+    written (16n)."""
+    return 16.0 * A + 56.0 * n
+
+
+def _roof(bytes_per_launch, launch_ms, peak, peak_kind, kernel):
+    achieved = bytes_per_launch / (launch_ms / 1e3) / 1e9 if launch_ms > 0 else 0.0
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": kernel, "peak_kind": peak_kind,
+            "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": launch_ms}
+
+
+def extension_legs(nk, torch, g, n, A, m, k, B, opts, stats, sseed, args, flush, stream, ev0, ev1, cfg):
+    import numpy as np
+    peak, peak_kind = measured_peaks()
+    legs = {}
+    cpu_s = max(1.0, args.cpu_seconds / 4)
+    ora = None
+    if not args.no_cpu:
+        import oracle
+        _, rp_o, col_o = oracle.generate(cfg["kind"], cfg["size"], GRAPH_SEED, **cfg["params"])
+        src_o = oracle.sample_sources(n, sseed, k)
+        ora = (oracle, rp_o, col_o, src_o)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ms, kern, launches = [], 0.0, 0
+        for _ in range(reps):
+            flush.zero_()
+            ev0.record(stream)
+            fn()
+            ev1.record(stream)
+            ev1.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+            st = nk.last_run_stats()
+            kern += st["kernel_ms"]
+            launches += st["launches"]
+        return sum(ms) / len(ms), kern / max(launches, 1), nk.last_run_stats()
+
+    def cpu_leg(fn_units, what):
+        """fn_units(j) runs the oracle on the first j units and returns m-traversals done."""
+        t0 = time.perf_counter()
+        done, j = 0, 1
+        while time.perf_counter() - t0 < cpu_s:
+            done += fn_units(j)
+            j = min(2 * j, 64)
+        t = time.perf_counter() - t0
+        return {"value": done / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"{what}, {t:.1f} s on 1 host core"}
+
+    base = nk.RunOpts.from_buffer_copy(opts)
+    base.flags &= ~nk.RUN_CUDA_GRAPH
+    base.flags |= nk.RUN_TIME_KERNELS
+    reps = max(1, min(args.steps, 5))
+
+    # closeness (Table 1): forward sweep and level sums
+    far_d = torch.empty(n, dtype=torch.float64, device="cuda")
+    reach_d = torch.empty(n, dtype=torch.float64, device="cuda")
+    ms, lms, st = timed(lambda: nk.closeness_sampled(g, sseed, k, base, out=(far_d, reach_d)), reps)
+    leg = {"value": m * k / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms, "batch": B,
+           "roofline": _roof(closeness_bytes(n, A, B, st["max_depth"] + 1), lms, peak, peak_kind, f"k_batch<W={B // 64}> forward only"),
+           "form": "batched forward sweep, sampled sources, scale n/k"}
+    if ora:
+        o, rp_o, col_o, src_o = ora
+        pos = [0]
+
+        def run_c(j):
+            sl = src_o[pos[0] % k:][:j]
+            pos[0] += len(sl)
+            o.closeness_sources(rp_o, col_o, sl, 1.0)
+            return m * len(sl)
+        leg["cpu_baseline"] = cpu_leg(run_c, "closeness from the first sources of the same sample")
+    legs["closeness"] = leg
+    del far_d, reach_d
+
+    # edge betweenness (Section 4.3)
+    edge_d = torch.empty(A, dtype=torch.float64, device="cuda")
+    ms, lms, st = timed(lambda: nk.edge_betweenness_sampled(g, sseed, k, base, out=edge_d), reps)
+    leg = {"value": m * k / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms, "batch": B,
+           "roofline": _roof(edge_bytes(n, A, B), lms, peak, peak_kind, f"k_batch<W={B // 64}, EDGE>"),
+           "form": "batched sweeps with per-arc shares, sampled sources, scale n/(2k)"}
+    if ora:
+        o, rp_o, col_o, src_o = ora
+        pos = [0]
+
+        def run_e(j):
+            sl = src_o[pos[0] % k:][:j]
+            pos[0] += len(sl)
+            o.edge_betweenness_sources(rp_o, col_o, sl, 1.0)
+            return m * len(sl)
+        leg["cpu_baseline"] = cpu_leg(run_e, "edge betweenness from the first sources of the same sample")
+    legs["edge_betweenness"] = leg
+    del edge_d
+
+    # error-bounded estimate (Section 3.2), epsilon 0.01, delta 0.1
+    rk_eps, rk_delta = 0.01, 0.1
+    ro = nk.run_opts(mode=nk.MODE_BATCHED, batch=B, alpha=stats["alpha"], flags=nk.RUN_TIME_KERNELS)
+    rk_out = torch.empty(n, dtype=torch.float64, device="cuda")
+    _, rk_r, rk_vd = nk.betweenness_rk(g, rk_eps, rk_delta, sseed, ro, out=rk_out)
+    ms, lms, st = timed(lambda: nk.betweenness_rk(g, rk_eps, rk_delta, sseed, ro, out=rk_out), min(reps, 3))
+    leg = {"value": m * rk_r / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms, "epsilon": rk_eps,
+           "delta": rk_delta, "samples": rk_r, "vertex_diameter_bound": rk_vd, "batch": B,
+           "roofline": _roof(rk_bytes(n, A, B), lms, peak, peak_kind, f"k_batch<W={B // 64}> forward + walks"),
+           "form": "batched forward sweeps + one random path walk per sample"}
+    if ora:
+        o, rp_o, col_o, _ = ora
+
+        def run_r(j):
+            eps = 0.2 if j < 4 else 0.1
+            _, r, _ = o.betweenness_rk(rp_o, col_o, eps, rk_delta, sseed + j)
+            return m * r
+        leg["cpu_baseline"] = cpu_leg(run_r, "the oracle's estimate at epsilon 0.2 / 0.1 (same per-sample work)")
+    legs["rk_estimate"] = leg
+    del rk_out
+
+    # weighted betweenness (Sections 2.3, 3.4): weights 1..16, 256 of the sampled sources
+    wk, wmax = min(256, k), 16
+    nk.random_weights(g, 5, wmax)
+    wo = nk.run_opts(flags=nk.RUN_TIME_KERNELS)
+    w_out = torch.empty(n, dtype=torch.float64, device="cuda")
+    ms, lms, st = timed(lambda: nk.betweenness_weighted_sampled(g, sseed, wk, wo, out=w_out), min(reps, 3))
+    leg = {"value": m * wk / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms, "k": wk, "wmax": wmax,
+           "buckets_max": st["max_depth"],
+           "roofline": _roof(weighted_bytes(n, A), lms, peak, peak_kind, "k_wsource (one source per launch)"),
+           "form": "per-source Dijkstra sweeps by distance buckets, sampled sources, scale n/(2k)"}
+    if ora:
+        o, rp_o, col_o, src_o = ora
+        w_o = o.edge_weights(rp_o, col_o, 5, wmax)
+        pos = [0]
+
+        def run_w(j):
+            sl = src_o[pos[0] % k:][:j]
+            pos[0] += len(sl)
+            o.betweenness_weighted_sources(rp_o, col_o, w_o, sl, 1.0)
+            return m * len(sl)
+        leg["cpu_baseline"] = cpu_leg(run_w, "weighted Brandes from the first sources of the same sample")
+    legs["weighted"] = leg
+    return legs
+
+
 # ------------------------------------------------------------------ reference arm
 def run_reference(args, world, rank):
     if rank != 0:
@@ -434,105 +598,12 @@ def run_ours(args, world, rank, local):
         out["cuda_graph"] = {"value": world * m * k * args.steps / (gtot / 1e3) / 1e9, "unit": UNIT,
                              "ms_per_step": gtot / args.steps}
 
-    # ---- closeness from the same sources: the forward sweep alone (Table 1, closeness
-    #      and its sampled estimate), device outputs
-    if not exact and rank == 0:
-        far_d = torch.empty(n, dtype=torch.float64, device="cuda")
-        reach_d = torch.empty(n, dtype=torch.float64, device="cuda")
-        co = nk.RunOpts.from_buffer_copy(opts)
-        co.flags &= ~nk.RUN_CUDA_GRAPH
-        for _ in range(max(args.warmup, 1)):
-            nk.closeness_sampled(g, sseed, k, co, out=(far_d, reach_d))
-        torch.cuda.synchronize()
-        cms, ckern, claunch = [], 0.0, 0
-        for _ in range(args.steps):
-            flush.zero_()
-            ev0.record(stream)
-            nk.closeness_sampled(g, sseed, k, co, out=(far_d, reach_d))
-            ev1.record(stream)
-            ev1.synchronize()
-            cms.append(ev0.elapsed_time(ev1))
-            cs = nk.last_run_stats()
-            ckern += cs["kernel_ms"]
-            claunch += cs["launches"]
-        ctot = sum(cms)
-        out["closeness"] = {"value": m * k * args.steps / (ctot / 1e3) / 1e9, "unit": UNIT,
-                            "ms_per_step": ctot / args.steps,
-                            "avg_launch_ms": ckern / max(claunch, 1), "batch": B,
-                            "form": "batched forward sweep, sampled sources, scale n/k"}
-
-    # ---- edge betweenness from the same sources (Section 4.3): the same two sweeps with a
-    #      per-arc share in the backward gather, device output of A doubles
-    if not exact and rank == 0:
-        edge_d = torch.empty(A, dtype=torch.float64, device="cuda")
-        eo = nk.RunOpts.from_buffer_copy(opts)
-        eo.flags &= ~nk.RUN_CUDA_GRAPH
-        for _ in range(max(args.warmup, 1)):
-            nk.edge_betweenness_sampled(g, sseed, k, eo, out=edge_d)
-        torch.cuda.synchronize()
-        ems, ekern, elaunch = [], 0.0, 0
-        for _ in range(args.steps):
-            flush.zero_()
-            ev0.record(stream)
-            nk.edge_betweenness_sampled(g, sseed, k, eo, out=edge_d)
-            ev1.record(stream)
-            ev1.synchronize()
-            ems.append(ev0.elapsed_time(ev1))
-            es = nk.last_run_stats()
-            ekern += es["kernel_ms"]
-            elaunch += es["launches"]
-        etot = sum(ems)
-        out["edge_betweenness"] = {"value": m * k * args.steps / (etot / 1e3) / 1e9, "unit": UNIT,
-                                   "ms_per_step": etot / args.steps,
-                                   "avg_launch_ms": ekern / max(elaunch, 1), "batch": B,
-                                   "form": "batched sweeps with per-arc shares, sampled sources, scale n/(2k)"}
-        del edge_d
-
-    # ---- error-bounded estimate after Riondato-Kornaropoulos (Section 3.2) on the same graph:
-    #      epsilon 0.01, delta 0.1; r sampled pairs, one forward sweep and one path walk each
-    if not exact and rank == 0:
-        rk_eps, rk_delta = 0.01, 0.1
-        ro = nk.run_opts(mode=nk.MODE_BATCHED, batch=B, alpha=stats["alpha"], flags=nk.RUN_TIME_KERNELS)
-        rk_out = torch.empty(n, dtype=torch.float64, device="cuda")
-        _, rk_r, rk_vd = nk.betweenness_rk(g, rk_eps, rk_delta, sseed, ro, out=rk_out)
-        torch.cuda.synchronize()
-        rms = []
-        for _ in range(max(1, min(args.steps, 3))):
-            flush.zero_()
-            ev0.record(stream)
-            nk.betweenness_rk(g, rk_eps, rk_delta, sseed, ro, out=rk_out)
-            ev1.record(stream)
-            ev1.synchronize()
-            rms.append(ev0.elapsed_time(ev1))
-        rtot = sum(rms)
-        out["rk_estimate"] = {"value": m * rk_r * len(rms) / (rtot / 1e3) / 1e9, "unit": UNIT,
-                              "ms_per_step": rtot / len(rms), "epsilon": rk_eps, "delta": rk_delta,
-                              "samples": rk_r, "vertex_diameter_bound": rk_vd, "batch": B,
-                              "form": "batched forward sweeps + one random path walk per sample"}
-
-    # ---- weighted betweenness (Sections 2.3, 3.4): the same graph with symmetric random
-    #      integer weights 1..16, Dijkstra sweeps by distance buckets, 256 of the sampled sources
-    if not exact and rank == 0:
-        wk = min(256, k)
-        nk.random_weights(g, 5, 16)
-        wo = nk.run_opts(flags=nk.RUN_TIME_KERNELS)
-        w_out = torch.empty(n, dtype=torch.float64, device="cuda")
-        nk.betweenness_weighted_sampled(g, sseed, wk, wo, out=w_out)
-        torch.cuda.synchronize()
-        wms = []
-        for _ in range(max(1, min(args.steps, 3))):
-            flush.zero_()
-            ev0.record(stream)
-            nk.betweenness_weighted_sampled(g, sseed, wk, wo, out=w_out)
-            ev1.record(stream)
-            ev1.synchronize()
-            wms.append(ev0.elapsed_time(ev1))
-        ws_ = nk.last_run_stats()
-        wtot = sum(wms)
-        out["weighted"] = {"value": m * wk * len(wms) / (wtot / 1e3) / 1e9, "unit": UNIT,
-                           "ms_per_step": wtot / len(wms), "k": wk, "wmax": 16,
-                           "buckets_max": ws_["max_depth"],
-                           "form": "per-source Dijkstra sweeps by distance buckets, sampled sources, scale n/(2k)"}
+    # ---- the widened rows on the same graph and sources: closeness, edge betweenness, the
+    #      error-bounded estimate and weighted betweenness, each with its byte-model roofline
+    #      and the oracle timed on a bounded sample beside it
+    if not exact and rank == 0 and not args.no_ext:
+        out.update(extension_legs(nk, torch, g, n, A, m, k, B, opts, stats, sseed, args, flush,
+                                  stream, ev0, ev1, cfg))
 
     # ---- plain per-source form on the same workload (the baseline it beats)
     if not args.no_per_source and rank == 0:
