@@ -180,11 +180,9 @@ def committed_traffic(config, batch):
     try:
         with open(prof) as f:
             pj = json.load(f)
-        if pj.get("batch") != batch:
-            return None
         if pj.get("kernel_source_sha256") != kernel_source_hash(pj["kernel_sources"]):
             return None
-        return pj.get("dram_bytes_per_launch")
+        return pj.get("by_batch", {}).get(str(batch), {}).get("dram_bytes_per_launch")
     except Exception:
         return None
 
