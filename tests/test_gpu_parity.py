@@ -515,3 +515,27 @@ def test_weighted_overflow_and_device_output(nk):
     out = torch.full((500,), -1.0, dtype=torch.float64, device="cuda")
     nk.betweenness_weighted_sampled(g, 3, 40, None, out=out)
     assert close(out.cpu().numpy(), want)
+
+
+# ------------------------------------------------------------------ degenerate inputs of the widened rows
+@pytest.mark.parametrize("graph", [G.complete(1), G.disjoint_union(G.complete(1), G.complete(1), G.complete(1)),
+                                   G.path(2), G.star(3)])
+def test_widened_rows_on_degenerate_graphs(nk, graph):
+    g, rp, col = both(nk, graph)
+    n = len(rp) - 1
+    f0, r0 = oracle.closeness_exact(rp, col)
+    f1, r1 = nk.closeness_exact(g)
+    assert np.array_equal(f1, f0) and np.array_equal(r1, r0)
+    e = nk.edge_betweenness_exact(g)
+    assert len(e) == len(col) and close(e, oracle.edge_betweenness_exact(rp, col))
+    for m in (dict(mode=1), dict(mode=2, batch=64)):
+        assert close(nk.edge_betweenness_sampled(g, 1, n, nk.run_opts(**m)), oracle.edge_betweenness_exact(rp, col))
+    want, r, vd = oracle.betweenness_rk(rp, col, 0.3, 0.3, 2)
+    got, r1_, vd1 = nk.betweenness_rk(g, 0.3, 0.3, 2)
+    assert (r1_, vd1) == (r, vd) and np.array_equal(got, want)
+    nk.random_weights(g, 3, 4)
+    w = oracle.edge_weights(rp, col, 3, 4)
+    assert close(nk.betweenness_weighted_exact(g), oracle.betweenness_weighted_exact(rp, col, w))
+    d, sg = nk.sssp_weighted(g, n - 1)
+    d0, s0 = oracle.sssp_weighted(rp, col, w, n - 1)
+    assert np.array_equal(d, d0) and np.array_equal(sg, s0)
