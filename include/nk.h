@@ -154,7 +154,10 @@ typedef struct nk_run_opts {
     int32_t direction; /* NK_DIR_* */
     double alpha;      /* bottom-up when alpha * (frontier arcs) > (unvisited arcs); 0 = auto */
     uint32_t flags;    /* NK_RUN_* */
-    int32_t reserved[7];
+    int32_t grid_ctas; /* if > 0: persistent launches use at most this many CTAs (0 = all
+                          co-resident CTAs); fewer CTAs make each grid barrier cheaper for
+                          sweeps with little work per level */
+    int32_t reserved[6];
 } nk_run_opts;
 
 /* Statistics of the last betweenness call made by this thread. */

@@ -941,7 +941,7 @@ int choose_lcap(const nk_graph *g, int B, const DevBuf *ws)
     size_t budget = have > base.total ? (have - base.total) / 2 : 0;
     int64_t l = slab ? (int64_t)(budget / slab) - 2 : 1022;
     l = std::min<int64_t>(l, 1022);
-    l = std::min<int64_t>(l, (int64_t)g->n);
+    l = std::min<int64_t>(l, std::max<int64_t>(g->n, 4));  // a BFS has at most n levels; 4 at least
     return (int)std::max<int64_t>(l, 0);
 }
 

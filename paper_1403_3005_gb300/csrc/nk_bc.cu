@@ -40,6 +40,7 @@ RunCfg cfg_of(const nk_run_opts *o, const nk_graph *g)
         c.direction = o->direction;
         c.alpha = o->alpha;
         c.time_kernels = (o->flags & NK_RUN_TIME_KERNELS) != 0;
+        c.grid_ctas = o->grid_ctas;
     }
     if (c.alpha <= 0 && g->tuned.valid) c.alpha = g->tuned.alpha;
     return c;
@@ -52,6 +53,7 @@ int check_cfg(const RunCfg &c)
     if (c.batch != 0 && c.batch != 64 && c.batch != 128 && c.batch != 256) return set_error(NK_ERR_ARG, "batch must be 0, 64, 128 or 256");
     if (c.tpv != 0 && (c.tpv < 1 || c.tpv > 32 || (c.tpv & (c.tpv - 1)))) return set_error(NK_ERR_ARG, "tpv must be 0 or a power of two <= 32");
     if (!(c.alpha >= 0)) return set_error(NK_ERR_ARG, "alpha must be >= 0");
+    if (c.grid_ctas < 0) return set_error(NK_ERR_ARG, "grid_ctas must be >= 0");
     return NK_OK;
 }
 
@@ -99,7 +101,7 @@ int run_captured(nk_graph *g, uint64_t seed, int32_t k, double scale, double *d_
     cfg.ws = e.ws;
     const bool hit = e.valid && e.seed == seed && e.k == k && e.batch == cfg.batch &&
                      e.alpha == cfg.alpha && e.dir == cfg.direction && e.scores == d_scores &&
-                     e.scale == scale;
+                     e.scale == scale && e.grid_ctas == cfg.grid_ctas;
     if (!hit) {
         e.reset();
         NK_TRY(e.src.ensure(sizeof(int32_t) * k));
@@ -142,6 +144,7 @@ int run_captured(nk_graph *g, uint64_t seed, int32_t k, double scale, double *d_
         e.dir = cfg.direction;
         e.scores = d_scores;
         e.scale = scale;
+        e.grid_ctas = cfg.grid_ctas;
         e.nb = nb;
         e.launches = captured;
     }

@@ -88,7 +88,7 @@ struct CapturedRun {
     bool valid = false;
     uint64_t seed = 0;
     int32_t k = 0;
-    int batch = 0, dir = 0;
+    int batch = 0, dir = 0, grid_ctas = 0;
     double alpha = 0, scale = 0;
     double *scores = nullptr;
     DevBuf ws[8];
