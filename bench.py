@@ -427,8 +427,10 @@ def extension_legs(nk, torch, g, n, A, m, k, B, opts, stats, sseed, args, flush,
     ms, lms, st = timed(lambda: nk.betweenness_weighted_sampled(g, sseed, wk, wo, out=w_out), min(reps, 3))
     leg = {"value": m * wk / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms, "k": wk, "wmax": wmax,
            "buckets_max": st["max_depth"],
-           "roofline": _roof(weighted_bytes(n, A), lms, peak, peak_kind, "k_wsource (one source per launch)"),
-           "form": "per-source Dijkstra sweeps by distance buckets, sampled sources, scale n/(2k)"}
+           "groups": st["batch"], "ctas_per_search": st["tpv"],
+           "roofline": _roof(weighted_bytes(n, A) * wk / max(1, st["launches"]), lms, peak, peak_kind,
+                             "k_wsource (searches side by side in CTA groups)"),
+           "form": "Dijkstra sweeps by distance buckets, one per CTA group, sampled sources, scale n/(2k)"}
     if ora:
         o, rp_o, col_o, src_o = ora
         w_o = o.edge_weights(rp_o, col_o, 5, wmax)
