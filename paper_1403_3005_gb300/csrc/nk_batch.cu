@@ -251,12 +251,23 @@ __device__ __forceinline__ void gather(const BArgs &a, int beg, int end,
                     e0 = dev::ff_add(e0, dev::ff_mul(sv[k], dev::ff_unpack(x0[k])));
                     e1 = dev::ff_add(e1, dev::ff_mul(sv[k], dev::ff_unpack(x1[k])));
                 }
-                e0 = dev::group_sum_ff<32>(e0);
-                e1 = dev::group_sum_ff<32>(e1);
-                if (lane == 0) {
-                    a.edge[base + s0] += dev::ff_to_double(e0);
-                    if (two) a.edge[base + s1] += dev::ff_to_double(e1);
+                // both sums at once: one exchange leaves neighbour 0's partials in the low
+                // half-warp and neighbour 1's in the high half, then each half reduces alone
+                const bool lo = lane < 16;
+                dev::ff mine = lo ? e0 : e1, other = lo ? e1 : e0;
+                dev::ff recv;
+                recv.hi = __shfl_xor_sync(FULL, other.hi, 16);
+                recv.lo = __shfl_xor_sync(FULL, other.lo, 16);
+                mine = dev::ff_add(mine, recv);
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) {
+                    dev::ff y;
+                    y.hi = __shfl_xor_sync(FULL, mine.hi, o);
+                    y.lo = __shfl_xor_sync(FULL, mine.lo, o);
+                    mine = dev::ff_add(mine, y);
                 }
+                if (lane == 0) a.edge[base + s0] += dev::ff_to_double(mine);
+                if (two && lane == 16) a.edge[base + s1] += dev::ff_to_double(mine);
             }
         }
     }
