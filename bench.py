@@ -53,7 +53,7 @@ GRAPH_SEED, SAMPLE_SEED = 1, 2
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--config", default="rmat18", choices=sorted(CONFIGS))
@@ -187,6 +187,9 @@ def committed_traffic(config, batch):
         return None
 
 
+NOMINAL_HBM_GBS = 7900.0  # HBM3e nominal bandwidth of one GB300
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -311,7 +314,7 @@ def weighted_bytes(n, A):
 def _roof(bytes_per_launch, launch_ms, peak, peak_kind, kernel):
     achieved = bytes_per_launch / (launch_ms / 1e3) / 1e9 if launch_ms > 0 else 0.0
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": kernel, "peak_kind": peak_kind,
+            "frac_nominal": achieved / NOMINAL_HBM_GBS, "traffic": None, "kernel": kernel, "peak_kind": peak_kind,
             "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": launch_ms}
 
 
@@ -561,7 +564,7 @@ def run_ours(args, world, rank, local):
     achieved = alg / (per_launch_ms / 1e3) / 1e9
     traffic = committed_traffic(args.config, B)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
+                "frac": achieved / peak, "frac_nominal": achieved / NOMINAL_HBM_GBS, "traffic": traffic,
                 "kernel": f"k_batch<W={B // 64}>", "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": alg, "avg_launch_ms": per_launch_ms}
 
