@@ -76,6 +76,7 @@ def _load():
             "or_betweenness_weighted": (ctypes.c_int, [i32, P, P, P, i32, P, dbl, P]),
             "or_rk_sample_count": (i64, [dbl, dbl, i32]),
             "or_rk_path": (i32, [i32, P, P, u64, i64, P, P]),
+            "or_rk_counts": (ctypes.c_int, [i32, P, P, u64, i64, i64, P]),
             "or_betweenness_rk": (ctypes.c_int, [i32, P, P, dbl, dbl, u64, P, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -280,6 +281,17 @@ def rk_path(rp, col, seed: int, i: int):
     if L < -1:
         raise OracleError(L, "rk_path")
     return int(uv[0]), int(uv[1]), (None if L == -1 else path[:L].copy())
+
+
+def rk_counts(rp, col, seed: int, i0: int, i1: int) -> np.ndarray:
+    """Interior-vertex counts of samples i0 <= i < i1 (uint64[n])."""
+    rp, col = _i32(rp), _i32(col)
+    n = len(rp) - 1
+    out = np.zeros(n, np.uint64)
+    rc = _load().or_rk_counts(n, _p(rp), _p(col), seed, i0, i1, _p(out))
+    if rc:
+        raise OracleError(rc, "rk_counts")
+    return out
 
 
 def betweenness_rk(rp, col, eps: float, delta: float, seed: int):

@@ -653,6 +653,25 @@ int32_t or_rk_path(int32_t n, const int32_t *row_ptr, const int32_t *col, uint64
     return rc != OR_OK ? rc : len;
 }
 
+/* counts[w] += number of the samples i0 <= i < i1 whose path has w as an interior vertex
+ * (samples are independent, so ranges can be computed apart and added) */
+int or_rk_counts(int32_t n, const int32_t *row_ptr, const int32_t *col, uint64_t seed, int64_t i0,
+                 int64_t i1, uint64_t *counts)
+{
+    if (n < 2 || i0 < 0 || i1 < i0) return OR_ERR_ARG;
+    int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *path = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    uint64_t *sigma = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
+    int rc = (dist && queue && path && sigma) ? OR_OK : OR_ERR_NOMEM;
+    for (int64_t i = i0; rc == OR_OK && i < i1; ++i) {
+        int32_t len = or_rk_one(n, row_ptr, col, seed, i, dist, sigma, queue, path, NULL, &rc);
+        for (int32_t p = 0; rc == OR_OK && p < len; ++p) counts[path[p]] += 1;
+    }
+    free(dist); free(queue); free(path); free(sigma);
+    return rc;
+}
+
 int or_betweenness_rk(int32_t n, const int32_t *row_ptr, const int32_t *col, double eps,
                       double delta, uint64_t seed, double *scores, int64_t *r_out, int32_t *vd_out)
 {

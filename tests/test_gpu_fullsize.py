@@ -101,3 +101,61 @@ def test_rmat24_properties(nk):
         tot += int(np.sum(r - 1))
     part = nk.betweenness_sources(g, src[:16], 1.0, nk.run_opts(mode=nk.MODE_BATCHED, batch=64))
     assert np.isclose(part.sum(), tot, rtol=1e-9)
+
+
+# ------------------------------------------------------------------ the widened rows at full size
+def _slices(fn, items, threads=None):
+    """The oracle on slices of `items` in host threads (the calls release the GIL)."""
+    import concurrent.futures as cf
+    import os
+    t = threads or max(2, min(16, os.cpu_count() or 2))
+    parts = [p for p in np.array_split(items, t) if len(p)]
+    with cf.ThreadPoolExecutor(len(parts)) as ex:
+        return list(ex.map(fn, parts))
+
+
+@pytest.fixture(scope="module")
+def rmat18(nk):
+    g = nk.graph_generate("rmat", 18, 1)
+    n, rp, col = oracle.generate("rmat", 18, 1)
+    return g, n, rp, col, nk.autotune(g, 2, 1024)
+
+
+def test_rmat18_closeness_k1024_full_vector(nk, rmat18):
+    g, n, rp, col, opts = rmat18
+    far, reach = nk.closeness_sampled(g, 2, 1024, opts)
+    src = oracle.sample_sources(n, 2, 1024)
+    parts = _slices(lambda p: oracle.closeness_sources(rp, col, p, 1.0), src)
+    scale = n / 1024
+    assert np.array_equal(far, sum(p[0] for p in parts) * scale)
+    assert np.array_equal(reach, sum(p[1] for p in parts) * scale)
+
+
+def test_rmat18_edge_betweenness_k1024_full_vector(nk, rmat18):
+    g, n, rp, col, opts = rmat18
+    got = nk.edge_betweenness_sampled(g, 2, 1024, opts)
+    src = oracle.sample_sources(n, 2, 1024)
+    want = sum(_slices(lambda p: oracle.edge_betweenness_sources(rp, col, p, 1.0), src)) * (n / (2.0 * 1024))
+    assert close(got, want)
+
+
+def test_rmat18_rk_estimate_full_counts(nk, rmat18):
+    # the bench leg runs epsilon 0.01; here epsilon 0.03 keeps the oracle's share in seconds
+    g, n, rp, col, opts = rmat18
+    ro = nk.run_opts(mode=nk.MODE_BATCHED, batch=opts.batch, alpha=opts.alpha)
+    got, r, vd = nk.betweenness_rk(g, 0.03, 0.1, 2, ro)
+    assert vd == oracle.vertex_diameter_estimate(rp, col) and r == oracle.rk_sample_count(0.03, 0.1, vd)
+    cuts = np.linspace(0, r, 17).astype(np.int64)
+    counts = sum(_slices(lambda p: sum(oracle.rk_counts(rp, col, 2, int(cuts[i]), int(cuts[i + 1])) for i in p),
+                         np.arange(16)))
+    assert np.array_equal(got, counts.astype(np.float64) * (n * (n - 1) / (2.0 * r)))
+
+
+def test_rmat18_weighted_k256_full_vector(nk, rmat18):
+    g, n, rp, col, _ = rmat18
+    nk.random_weights(g, 5, 16)
+    w = oracle.edge_weights(rp, col, 5, 16)
+    got = nk.betweenness_weighted_sampled(g, 2, 256)
+    src = oracle.sample_sources(n, 2, 256)
+    want = sum(_slices(lambda p: oracle.betweenness_weighted_sources(rp, col, w, p, 1.0), src)) * (n / (2.0 * 256))
+    assert close(got, want)

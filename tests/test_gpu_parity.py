@@ -539,3 +539,19 @@ def test_widened_rows_on_degenerate_graphs(nk, graph):
     d, sg = nk.sssp_weighted(g, n - 1)
     d0, s0 = oracle.sssp_weighted(rp, col, w, n - 1)
     assert np.array_equal(d, d0) and np.array_equal(sg, s0)
+
+
+def test_grid_ctas_option_parity_and_determinism(nk):
+    g, rp, col, w = weighted_both(nk, SMALL["hubs"], 11, 6)
+    n = len(rp) - 1
+    want = oracle.betweenness_weighted_sampled(rp, col, w, 3, 300)
+    runs = [nk.betweenness_weighted_sampled(g, 3, 300, nk.run_opts(grid_ctas=gc)) for gc in (0, 0, 1, 7, 40)]
+    assert np.array_equal(runs[0], runs[1])          # the same groups sum in the same order
+    for r in runs:
+        assert close(r, want)
+    vb = oracle.betweenness_sampled(rp, col, 3, 300)
+    for m in (dict(mode=1, grid_ctas=5), dict(mode=2, batch=64, grid_ctas=9), dict(mode=2, batch=256, grid_ctas=2)):
+        assert close(nk.betweenness_sampled(g, 3, 300, nk.run_opts(**m)), vb), m
+    with pytest.raises(nk.NkError) as e:
+        nk.betweenness_sampled(g, 3, 300, nk.run_opts(grid_ctas=-1))
+    assert e.value.rc == nk.ERR_ARG

@@ -781,3 +781,11 @@ def test_weighted_sampled_k_equals_n():
     w = oracle.edge_weights(rp, col, 5, 10)
     assert np.array_equal(oracle.betweenness_weighted_sampled(rp, col, w, 8, n),
                           oracle.betweenness_weighted_exact(rp, col, w))
+
+
+def test_rk_counts_in_ranges_add_up_to_the_estimate():
+    n, rp, col = oracle.generate("er", 300, 6, avg_deg=5.0)
+    sc, r, vd = oracle.betweenness_rk(rp, col, 0.1, 0.1, 4)
+    cuts = [0, 7, 100, r // 2, r]
+    counts = sum(oracle.rk_counts(rp, col, 4, a, b) for a, b in zip(cuts[:-1], cuts[1:]))
+    assert np.array_equal(counts.astype(np.float64) * (n * (n - 1) / (2.0 * r)), sc)
