@@ -349,12 +349,16 @@ __device__ __forceinline__ void for_level(const BArgs &a, int qo, int nq,
         return __shfl_sync(FULL, e, 0) != 0;
     };
     if (qo >= 0) {
+        // up to kGrabQ entries per grab, fewer when the level is short (level 0, deep
+        // levels), so that its entries spread over many warps
+        const long long nwq = ((long long)gridDim.x * blockDim.x) >> 5;
+        const int gq = (int)max(1LL, min((long long)kGrabQ, (long long)nq / nwq));
         for (;;) {
             int i0 = 0;
-            if (lane == 0) i0 = atomicAdd(ctr, kGrabQ);
+            if (lane == 0) i0 = atomicAdd(ctr, gq);
             i0 = __shfl_sync(FULL, i0, 0);
             if (i0 >= nq || expired()) break;
-            const int i1 = min(i0 + kGrabQ, nq);
+            const int i1 = min(i0 + gq, nq);
             for (int i = i0; i < i1; ++i) {
                 const int v = __ldcg(a.queue + qo + i);
                 if ((unsigned)v >= (unsigned)a.n) {  // warp-uniform
