@@ -574,9 +574,11 @@ int nk_graph_random_weights(nk_graph *g, uint64_t seed, int32_t wmax)
     return random_weights(g, seed, wmax, stream());
 }
 
-int nk_graph_export_weights(const nk_graph *g, int32_t *w)
+int nk_graph_export_weights(const nk_graph *gc, int32_t *w)
 {
-    if (!g || !w) return set_error(NK_ERR_ARG, "graph or output is null");
+    if (!gc || !w) return set_error(NK_ERR_ARG, "graph or output is null");
+    nk_graph *g = const_cast<nk_graph *>(gc);
+    std::lock_guard<std::mutex> lock(g->mu);
     if (!g->weighted) return set_error(NK_ERR_ARG, "the graph has no weights");
     cudaStream_t s = stream();
     if (g->A > 0) NK_CUDA(cudaMemcpyAsync(w, g->wt.p, sizeof(int32_t) * (size_t)g->A, cudaMemcpyDeviceToHost, s));
