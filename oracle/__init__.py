@@ -46,44 +46,47 @@ def build(force: bool = False) -> str:
     return _OUT
 
 
+def _bind(lib):
+    """Declares the C signatures on a loaded copy of the oracle library."""
+    i32, i64, u64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    P = ctypes.c_void_p
+    sig = {
+        "or_mix64": (u64, [u64]),
+        "or_stream": (u64, [u64, u64]),
+        "or_log": (dbl, [dbl]),
+        "or_gen_er": (i64, [i32, dbl, u64, P, P, i64]),
+        "or_gen_ba": (i64, [i32, i32, u64, P, P, i64]),
+        "or_gen_rmat": (i64, [i32, i32, dbl, dbl, dbl, u64, P, P, i64]),
+        "or_csr_build": (i64, [i32, i64, P, P, P, P]),
+        "or_sample_sources": (ctypes.c_int, [i32, u64, i32, P]),
+        "or_bfs": (ctypes.c_int, [i32, P, P, i32, P, P]),
+        "or_dependencies": (ctypes.c_int, [i32, P, P, i32, P]),
+        "or_betweenness": (ctypes.c_int, [i32, P, P, i32, P, dbl, P]),
+        "or_betweenness_exact": (ctypes.c_int, [i32, P, P, P]),
+        "or_betweenness_sampled": (ctypes.c_int, [i32, P, P, u64, i32, P]),
+        "or_closeness": (ctypes.c_int, [i32, P, P, i32, P, dbl, P, P]),
+        "or_edge_betweenness": (ctypes.c_int, [i32, P, P, i32, P, dbl, P]),
+        "or_vertex_diameter_estimate": (ctypes.c_int, [i32, P, P, P]),
+        "or_edge_weights": (ctypes.c_int, [i32, P, P, u64, i32, P]),
+        "or_sssp_weighted": (ctypes.c_int, [i32, P, P, P, i32, P, P]),
+        "or_betweenness_weighted": (ctypes.c_int, [i32, P, P, P, i32, P, dbl, P]),
+        "or_rk_sample_count": (i64, [dbl, dbl, i32]),
+        "or_rk_path": (i32, [i32, P, P, u64, i64, P, P]),
+        "or_rk_counts": (ctypes.c_int, [i32, P, P, u64, i64, i64, P]),
+        "or_betweenness_rk": (ctypes.c_int, [i32, P, P, dbl, dbl, u64, P, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype, f.argtypes = res, args
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
-        if _lib is not None:
-            return _lib
-        lib = ctypes.CDLL(build())
-        i32, i64, u64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
-        P = ctypes.c_void_p
-        sig = {
-            "or_mix64": (u64, [u64]),
-            "or_stream": (u64, [u64, u64]),
-            "or_log": (dbl, [dbl]),
-            "or_gen_er": (i64, [i32, dbl, u64, P, P, i64]),
-            "or_gen_ba": (i64, [i32, i32, u64, P, P, i64]),
-            "or_gen_rmat": (i64, [i32, i32, dbl, dbl, dbl, u64, P, P, i64]),
-            "or_csr_build": (i64, [i32, i64, P, P, P, P]),
-            "or_sample_sources": (ctypes.c_int, [i32, u64, i32, P]),
-            "or_bfs": (ctypes.c_int, [i32, P, P, i32, P, P]),
-            "or_dependencies": (ctypes.c_int, [i32, P, P, i32, P]),
-            "or_betweenness": (ctypes.c_int, [i32, P, P, i32, P, dbl, P]),
-            "or_betweenness_exact": (ctypes.c_int, [i32, P, P, P]),
-            "or_betweenness_sampled": (ctypes.c_int, [i32, P, P, u64, i32, P]),
-            "or_closeness": (ctypes.c_int, [i32, P, P, i32, P, dbl, P, P]),
-            "or_edge_betweenness": (ctypes.c_int, [i32, P, P, i32, P, dbl, P]),
-            "or_vertex_diameter_estimate": (ctypes.c_int, [i32, P, P, P]),
-            "or_edge_weights": (ctypes.c_int, [i32, P, P, u64, i32, P]),
-            "or_sssp_weighted": (ctypes.c_int, [i32, P, P, P, i32, P, P]),
-            "or_betweenness_weighted": (ctypes.c_int, [i32, P, P, P, i32, P, dbl, P]),
-            "or_rk_sample_count": (i64, [dbl, dbl, i32]),
-            "or_rk_path": (i32, [i32, P, P, u64, i64, P, P]),
-            "or_rk_counts": (ctypes.c_int, [i32, P, P, u64, i64, i64, P]),
-            "or_betweenness_rk": (ctypes.c_int, [i32, P, P, dbl, dbl, u64, P, P, P]),
-        }
-        for name, (res, args) in sig.items():
-            f = getattr(lib, name)
-            f.restype, f.argtypes = res, args
-        _lib = lib
-        return lib
+        if _lib is None:
+            _lib = _bind(ctypes.CDLL(build()))
+        return _lib
 
 
 def _p(a: np.ndarray):

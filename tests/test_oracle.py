@@ -445,15 +445,17 @@ def test_ba_structure():
 
 
 def test_rmat_quadrant_frequencies():
-    scale, ef, a, b, c = 12, 16, 0.57, 0.19, 0.19
-    eu, ev = oracle.gen_rmat(scale, ef, a, b, c, 5)
-    assert len(eu) == ef << scale and eu.max() < 1 << scale and ev.max() < 1 << scale
-    E = len(eu)
-    for bit in (scale - 1, 0):
-        ru, rv = (eu >> bit) & 1, (ev >> bit) & 1
-        for (x, y), p in (((0, 0), a), ((0, 1), b), ((1, 0), c), ((1, 1), 1 - a - b - c)):
-            f = np.sum((ru == x) & (rv == y))
-            assert abs(f - E * p) < 5 * math.sqrt(E * p * (1 - p))
+    # the benchmark's parameters, and unequal b and c so that the (0,1) and (1,0) quadrants
+    # cannot be confused
+    for scale, ef, a, b, c in ((12, 16, 0.57, 0.19, 0.19), (11, 16, 0.45, 0.30, 0.10)):
+        eu, ev = oracle.gen_rmat(scale, ef, a, b, c, 5)
+        assert len(eu) == ef << scale and eu.max() < 1 << scale and ev.max() < 1 << scale
+        E = len(eu)
+        for bit in (scale - 1, 0):
+            ru, rv = (eu >> bit) & 1, (ev >> bit) & 1
+            for (x, y), p in (((0, 0), a), ((0, 1), b), ((1, 0), c), ((1, 1), 1 - a - b - c)):
+                f = np.sum((ru == x) & (rv == y))
+                assert abs(f - E * p) < 5 * math.sqrt(E * p * (1 - p))
     n, rp, col = oracle.generate("rmat", 10, 1)
     check_canonical(n, rp, col)
 
@@ -789,3 +791,26 @@ def test_rk_counts_in_ranges_add_up_to_the_estimate():
     cuts = [0, 7, 100, r // 2, r]
     counts = sum(oracle.rk_counts(rp, col, 4, a, b) for a, b in zip(cuts[:-1], cuts[1:]))
     assert np.array_equal(counts.astype(np.float64) * (n * (n - 1) / (2.0 * r)), sc)
+
+
+def test_edge_betweenness_single_source_bruteforce():
+    # one source s: the edge {u, v} scores sum_t sigma_st({u, v}) / sigma_st on both of its arcs
+    # (a sum over one source is not symmetric in the edge's direction, unlike a sum over all)
+    from bruteforce import adjacency, enumerate_shortest_paths
+    for g in (G.gnp(9, 0.4, 3), G.grid(3, 4), G.disjoint_union(G.cycle(6), G.star(4))):
+        n, rp, col = csr(g)
+        adj = adjacency(*g)
+        for s in range(n):
+            ref = {}
+            for t in range(n):
+                if t == s:
+                    continue
+                ps = enumerate_shortest_paths(adj, s, t)
+                for p in ps:
+                    for x, y in zip(p[:-1], p[1:]):
+                        key = (min(x, y), max(x, y))
+                        ref[key] = ref.get(key, Fraction(0)) + Fraction(1, len(ps))
+            e = oracle.edge_betweenness_sources(rp, col, np.array([s], np.int32), 1.0)
+            ev = edge_values(n, rp, col, e)
+            for key, val in ev.items():
+                assert math.isclose(val, float(ref.get(key, 0)), rel_tol=1e-12, abs_tol=1e-12), (s, key)
