@@ -55,7 +55,7 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int kTraceCap = 1024;
 constexpr int kChunk = kHeavyChunk;  // arcs per work item; longer rows are split
 constexpr int kGrabQ = 8;            // queue entries a warp takes at a time
-constexpr int kGrabV = 64;           // vertices a warp scans at a time
+constexpr int kGrabV = 32;           // vertices a warp scans at a time (one ballot window)
 constexpr int kGrabCMax = 16;        // most heavy chunks a warp takes at a time
 // work-counter slots of a level
 enum { WQ_BU = 0, WQ_BU_C, WQ_PUSH, WQ_PUSH_C, WQ_PULL, WQ_PULL_C, WQ_BACK, WQ_BACK_C };
