@@ -157,7 +157,10 @@ typedef struct nk_run_opts {
     int32_t grid_ctas; /* if > 0: persistent launches use at most this many CTAs (0 = all
                           co-resident CTAs); fewer CTAs make each grid barrier cheaper for
                           sweeps with little work per level */
-    int32_t reserved[6];
+    int32_t chunk;     /* batched mode: rows longer than this many arcs are split into chunks
+                          of this many arcs, each taken by its own warp; a multiple of 32 in
+                          [32, 4096], or 0 for 256 (or the autotuner's choice) */
+    int32_t reserved[5];
 } nk_run_opts;
 
 /* Statistics of the last betweenness call made by this thread. */

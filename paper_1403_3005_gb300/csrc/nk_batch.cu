@@ -53,7 +53,7 @@ constexpr int kErrCheck = 101;  // internal status: a device-side range check fa
 constexpr int kStartLevels = 48; // level slabs of a first attempt
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kTraceCap = 1024;
-constexpr int kChunk = kHeavyChunk;  // arcs per work item; longer rows are split
+constexpr int kChunk = kHeavyChunk;  // default arcs per work item; longer rows are split
 constexpr int kGrabQ = 8;            // queue entries a warp takes at a time
 constexpr int kGrabV = 32;           // vertices a warp scans at a time (one ballot window)
 constexpr int kGrabCMax = 16;        // most heavy chunks a warp takes at a time
@@ -84,7 +84,9 @@ struct BArgs {
     uint64_t limit_ns;
     double alpha;
     int dir;
-    // vertices of degree > kChunk are split into chunks of kChunk arcs
+    // vertices of degree > chunk are split into chunks of `chunk` arcs (kChunk unless the
+    // caller or the autotuner chose another size)
+    int32_t chunk;
     const int32_t *hv;           // [H] heavy vertices
     const int32_t *hfirst;       // [H+1] first chunk of each heavy vertex
     const int32_t *chunk_h;      // [C] heavy index of each chunk
@@ -441,8 +443,8 @@ template <class Fn> __device__ __forceinline__ void for_chunks(const BArgs &a, i
         for (int c = c0; c < min(c0 + gc, a.C); ++c) {
             const int i = __ldg(a.chunk_h + c);
             const int h = __ldg(a.hv + i);
-            const int j0 = __ldg(a.rp + h) + (c - __ldg(a.hfirst + i)) * kChunk;
-            const int j1 = min(j0 + kChunk, __ldg(a.rp + h + 1));
+            const int j0 = __ldg(a.rp + h) + (c - __ldg(a.hfirst + i)) * a.chunk;
+            const int j1 = min(j0 + a.chunk, __ldg(a.rp + h + 1));
             fn(c, h, j0, j1);
         }
     }
@@ -465,7 +467,7 @@ __device__ __forceinline__ void store_part(const BArgs &a, int c, const unsigned
     for (int k = 0; k < 2 * W; ++k) row[32 * k] = acc[k];
 }
 
-__device__ __forceinline__ bool heavy(const BArgs &a, int v) { return deg_of(a.rp, v) > kChunk; }
+__device__ __forceinline__ bool heavy(const BArgs &a, int v) { return deg_of(a.rp, v) > a.chunk; }
 
 template <int W, bool EDGE>
 __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
@@ -911,14 +913,17 @@ struct Layout {
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// chunk count of the heavy table (an upper bound before the table is built)
-int64_t chunk_count(const nk_graph *g)
+// chunk count of the heavy table for `chunk` arcs per chunk (an upper bound before the
+// table is built)
+int64_t chunk_count(const nk_graph *g, int chunk)
 {
-    if (g->heavy_H >= 0) return g->heavy_C;
-    return g->A / kChunk + (g->max_deg > kChunk ? g->n : 0);
+    if (chunk <= 0) chunk = kChunk;
+    if (chunk == kChunk && g->heavy_H >= 0) return g->heavy_C;
+    if (chunk != kChunk && g->heavy_alt_H >= 0 && g->heavy_alt_chunk == chunk) return g->heavy_alt_C;
+    return g->A / chunk + (g->max_deg > chunk ? g->n : 0);
 }
 
-Layout layout(const nk_graph *g, int B, int lcap)
+Layout layout(const nk_graph *g, int B, int lcap, int chunk = 0)
 {
     Layout L;
     L.B = B;
@@ -940,17 +945,17 @@ Layout layout(const nk_graph *g, int B, int lcap)
     L.off_cnt = o;
     o = align_up(o + (size_t)(lcap + 3) * (3 * 4 + 2 * 8 + 8 * 4));
     L.off_part = o;
-    o = align_up(o + (size_t)chunk_count(g) * B * 8);
+    o = align_up(o + (size_t)chunk_count(g, chunk) * B * 8);
     L.total = o;
     return L;
 }
 
-int choose_lcap(const nk_graph *g, int B, const DevBuf *ws)
+int choose_lcap(const nk_graph *g, int B, const DevBuf *ws, int chunk = 0)
 {
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     const size_t slab = (size_t)g->n * (B / 64) * 8;
-    const Layout base = layout(g, B, 0);
+    const Layout base = layout(g, B, 0, chunk);
     // level slabs may use up to half of what is free after the rest of the batch state
     const size_t have = free_b + ws[5].bytes;
     size_t budget = have > base.total ? (have - base.total) / 2 : 0;
@@ -967,11 +972,12 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
                    const RunCfg &cfg, RunStats *st, cudaStream_t s)
 {
     constexpr int B = 64 * W;
-    NK_TRY(build_heavy(g, s));
+    HeavyView hw;
+    NK_TRY(heavy_view(g, cfg.chunk, s, &hw));
     DevBuf *ws = scratch(cfg, g);
     // level slabs: start small; batches whose BFS is deeper are rerun once with the
     // largest cap that free memory allows, then (if still deeper) by the per-source form
-    const int lmax = cfg.lcap > 0 ? std::min(cfg.lcap, std::max(g->n, 4)) : choose_lcap(g, B, ws);
+    const int lmax = cfg.lcap > 0 ? std::min(cfg.lcap, std::max(g->n, 4)) : choose_lcap(g, B, ws, hw.chunk);
     if (lmax < 4) return set_error(NK_ERR_NOMEM, "not enough device memory for a batch of %d sources", B);
     const int lstart = cfg.lcap > 0 ? lmax : std::min(lmax, std::max(kStartLevels, 4));
     const int nb = (k + B - 1) / B;
@@ -993,7 +999,7 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
         NK_CUDA(cudaMemsetAsync(trace_buf.p, 0, sizeof(unsigned long long) * 2 * kTraceCap, s));
     }
     for (int lcap = lstart;;) {
-        const Layout L = layout(g, B, lcap);
+        const Layout L = layout(g, B, lcap, hw.chunk);
         NK_TRY(ws[WS_BATCH].ensure(L.total));
         char *base = ws[WS_BATCH].as<char>();
         BArgs a;
@@ -1017,11 +1023,12 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
         a.qoff = a.qcnt + lv;
         a.wq = a.qoff + lv;
         a.scores = d_scores;
-        a.hv = g->heavy[0].as<int32_t>();
-        a.hfirst = g->heavy[1].as<int32_t>();
-        a.chunk_h = g->heavy[2].as<int32_t>();
-        a.H = g->heavy_H;
-        a.C = g->heavy_C;
+        a.hv = hw.hv;
+        a.hfirst = hw.hfirst;
+        a.chunk_h = hw.chunk_h;
+        a.H = hw.H;
+        a.C = hw.C;
+        a.chunk = hw.chunk;
         a.part = reinterpret_cast<unsigned long long *>(base + L.off_part);
         a.trace = nullptr;
         a.far = cfg.far;
@@ -1129,12 +1136,13 @@ int enqueue_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scor
 {
     constexpr int B = 64 * W;
     DevBuf *ws = scratch(cfg, g);
-    const int lcap = cfg.lcap > 0 ? std::min(cfg.lcap, std::max(g->n, 4)) : std::min(choose_lcap(g, B, ws), std::max(kStartLevels, 4));
+    HeavyView hw;
+    NK_TRY(heavy_view(g, cfg.chunk, s, &hw));
+    const int lcap = cfg.lcap > 0 ? std::min(cfg.lcap, std::max(g->n, 4)) : std::min(choose_lcap(g, B, ws, hw.chunk), std::max(kStartLevels, 4));
     if (lcap < 4) return set_error(NK_ERR_NOMEM, "not enough device memory for a batch of %d sources", B);
     const int nb = (k + B - 1) / B;
-    const Layout L = layout(g, B, lcap);
+    const Layout L = layout(g, B, lcap, hw.chunk);
     if (prepare_only) {
-        NK_TRY(build_heavy(g, s));
         NK_TRY(ws[WS_BATCH].ensure(L.total));
         NK_TRY(ws[WS_BCTRL].ensure(sizeof(Ctrl) * nb));
         if (blocks_per_sm<W>() < 1) return set_error(NK_ERR_CUDA, "batched kernel cannot be resident");
@@ -1168,11 +1176,12 @@ int enqueue_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scor
     a.qoff = a.qcnt + lv;
     a.wq = a.qoff + lv;
     a.scores = d_scores;
-    a.hv = g->heavy[0].as<int32_t>();
-    a.hfirst = g->heavy[1].as<int32_t>();
-    a.chunk_h = g->heavy[2].as<int32_t>();
-    a.H = g->heavy_H;
-    a.C = g->heavy_C;
+    a.hv = hw.hv;
+    a.hfirst = hw.hfirst;
+    a.chunk_h = hw.chunk_h;
+    a.H = hw.H;
+    a.C = hw.C;
+    a.chunk = hw.chunk;
     a.part = reinterpret_cast<unsigned long long *>(base + L.off_part);
     a.trace = nullptr;
     a.far = cfg.far;

@@ -41,8 +41,10 @@ RunCfg cfg_of(const nk_run_opts *o, const nk_graph *g)
         c.alpha = o->alpha;
         c.time_kernels = (o->flags & NK_RUN_TIME_KERNELS) != 0;
         c.grid_ctas = o->grid_ctas;
+        c.chunk = o->chunk;
     }
     if (c.alpha <= 0 && g->tuned.valid) c.alpha = g->tuned.alpha;
+    if (c.chunk == 0 && g->tuned.valid) c.chunk = g->tuned.chunk;
     return c;
 }
 
@@ -54,6 +56,8 @@ int check_cfg(const RunCfg &c)
     if (c.tpv != 0 && (c.tpv < 1 || c.tpv > 32 || (c.tpv & (c.tpv - 1)))) return set_error(NK_ERR_ARG, "tpv must be 0 or a power of two <= 32");
     if (!(c.alpha >= 0)) return set_error(NK_ERR_ARG, "alpha must be >= 0");
     if (c.grid_ctas < 0) return set_error(NK_ERR_ARG, "grid_ctas must be >= 0");
+    if (c.chunk != 0 && (c.chunk < 32 || c.chunk > 4096 || c.chunk % 32))
+        return set_error(NK_ERR_ARG, "chunk must be 0 or a multiple of 32 in [32, 4096]");
     return NK_OK;
 }
 
@@ -101,7 +105,7 @@ int run_captured(nk_graph *g, uint64_t seed, int32_t k, double scale, double *d_
     cfg.ws = e.ws;
     const bool hit = e.valid && e.seed == seed && e.k == k && e.batch == cfg.batch &&
                      e.alpha == cfg.alpha && e.dir == cfg.direction && e.scores == d_scores &&
-                     e.scale == scale && e.grid_ctas == cfg.grid_ctas;
+                     e.scale == scale && e.grid_ctas == cfg.grid_ctas && e.chunk == cfg.chunk;
     if (!hit) {
         e.reset();
         NK_TRY(e.src.ensure(sizeof(int32_t) * k));
@@ -145,6 +149,7 @@ int run_captured(nk_graph *g, uint64_t seed, int32_t k, double scale, double *d_
         e.scores = d_scores;
         e.scale = scale;
         e.grid_ctas = cfg.grid_ctas;
+        e.chunk = cfg.chunk;
         e.nb = nb;
         e.launches = captured;
     }
@@ -701,11 +706,12 @@ int nk_autotune(const nk_graph *gc, uint64_t seed, int32_t k, nk_run_opts *best)
     NK_TRY(dsrc.alloc(sizeof(int32_t) * k, s));
     NK_TRY(dsc.alloc(sizeof(double) * g->n, s));
     NK_TRY(sample_sources_device(g->n, seed, k, dsrc.as<int32_t>(), s));
-    auto trial = [&](int B, double alpha, double *ms_per_src) -> int {
+    auto trial = [&](int B, double alpha, double *ms_per_src, int chunk = 0) -> int {
         RunCfg c;
         c.mode = NK_MODE_BATCHED;
         c.batch = B;
         c.alpha = alpha;
+        c.chunk = chunk;
         c.time_kernels = true;
         const int32_t kk = std::min<int32_t>(ks, B);
         NK_CUDA(cudaMemsetAsync(dsc.p, 0, sizeof(double) * g->n, s));
@@ -737,13 +743,26 @@ int nk_autotune(const nk_graph *gc, uint64_t seed, int32_t k, nk_run_opts *best)
             bestA = alpha;
         }
     }
+    // hub chunks of 128 arcs instead of 256: better balanced levels on some graphs, more
+    // partial sums on others
+    int bestC = 0;
+    if (g->max_deg > 128) {
+        double t;
+        NK_TRY(trial(bestB, bestA, &t, 128));
+        if (t < bestT) {
+            bestT = t;
+            bestC = 128;
+        }
+    }
     g->tuned.valid = true;
     g->tuned.batch = bestB;
     g->tuned.alpha = bestA;
+    g->tuned.chunk = bestC;
     *best = nk_run_opts();
     best->mode = NK_MODE_BATCHED;
     best->batch = bestB;
     best->alpha = bestA;
+    best->chunk = bestC;
     return NK_OK;
 }
 

@@ -462,13 +462,11 @@ int build_csr_from_edges(nk_graph *g, int32_t n, int64_t m, const int32_t *d_u,
     return finish_graph(g, st, d_max);
 }
 
-// Chunk table of the vertices whose degree exceeds kHeavyChunk, built once per graph on the
-// host from row_ptr: heavy vertex ids, the first chunk of each, and the owner of every
-// chunk.  Returns the number of chunks (0 for graphs without heavy vertices).
-int build_heavy(nk_graph *g, cudaStream_t s)
+// Chunk table of the vertices whose degree exceeds `chunk`, built on the host from row_ptr:
+// heavy vertex ids, the first chunk of each, and the owner of every chunk.
+static int build_table(nk_graph *g, int chunk, nk::DevBuf (&dst)[3], int32_t &H, int32_t &C,
+                       std::vector<int32_t> *h_hv, std::vector<int32_t> *h_hfirst, cudaStream_t s)
 {
-    std::lock_guard<std::mutex> lk(g->heavy_mu);
-    if (g->heavy_H >= 0) return NK_OK;
     std::vector<int32_t> rp(g->n + 1);
     NK_CUDA(cudaMemcpyAsync(rp.data(), g->rp.p, sizeof(int32_t) * (g->n + 1), cudaMemcpyDeviceToHost, s));
     NK_CUDA(cudaStreamSynchronize(s));
@@ -476,27 +474,61 @@ int build_heavy(nk_graph *g, cudaStream_t s)
     int64_t c = 0;
     for (int32_t v = 0; v < g->n; ++v) {
         const int32_t deg = rp[v + 1] - rp[v];
-        if (deg <= kHeavyChunk) continue;
-        const int32_t nc = (deg + kHeavyChunk - 1) / kHeavyChunk;
+        if (deg <= chunk) continue;
+        const int32_t nc = (deg + chunk - 1) / chunk;
         hfirst.push_back((int32_t)c);
         for (int32_t j = 0; j < nc; ++j) chunk_h.push_back((int32_t)hv.size());
         hv.push_back(v);
         c += nc;
     }
     hfirst.push_back((int32_t)c);
-    NK_TRY(g->heavy[0].ensure(sizeof(int32_t) * std::max<size_t>(hv.size(), 1)));
-    NK_TRY(g->heavy[1].ensure(sizeof(int32_t) * hfirst.size()));
-    NK_TRY(g->heavy[2].ensure(sizeof(int32_t) * std::max<size_t>(chunk_h.size(), 1)));
+    NK_TRY(dst[0].ensure(sizeof(int32_t) * std::max<size_t>(hv.size(), 1)));
+    NK_TRY(dst[1].ensure(sizeof(int32_t) * hfirst.size()));
+    NK_TRY(dst[2].ensure(sizeof(int32_t) * std::max<size_t>(chunk_h.size(), 1)));
     if (!hv.empty()) {
-        NK_CUDA(cudaMemcpyAsync(g->heavy[0].p, hv.data(), sizeof(int32_t) * hv.size(), cudaMemcpyHostToDevice, s));
-        NK_CUDA(cudaMemcpyAsync(g->heavy[2].p, chunk_h.data(), sizeof(int32_t) * chunk_h.size(), cudaMemcpyHostToDevice, s));
+        NK_CUDA(cudaMemcpyAsync(dst[0].p, hv.data(), sizeof(int32_t) * hv.size(), cudaMemcpyHostToDevice, s));
+        NK_CUDA(cudaMemcpyAsync(dst[2].p, chunk_h.data(), sizeof(int32_t) * chunk_h.size(), cudaMemcpyHostToDevice, s));
     }
-    NK_CUDA(cudaMemcpyAsync(g->heavy[1].p, hfirst.data(), sizeof(int32_t) * hfirst.size(), cudaMemcpyHostToDevice, s));
+    NK_CUDA(cudaMemcpyAsync(dst[1].p, hfirst.data(), sizeof(int32_t) * hfirst.size(), cudaMemcpyHostToDevice, s));
     NK_CUDA(cudaStreamSynchronize(s));
-    g->heavy_C = (int32_t)c;
-    g->heavy_H = (int32_t)hv.size();
-    g->h_hv = std::move(hv);
-    g->h_hfirst = std::move(hfirst);
+    C = (int32_t)c;
+    H = (int32_t)hv.size();
+    if (h_hv) *h_hv = std::move(hv);
+    if (h_hfirst) *h_hfirst = std::move(hfirst);
+    return NK_OK;
+}
+
+// The graph's own table (kHeavyChunk arcs per chunk), built once.
+int build_heavy(nk_graph *g, cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lk(g->heavy_mu);
+    if (g->heavy_H >= 0) return NK_OK;
+    int32_t H = -1, C = 0;
+    NK_TRY(build_table(g, kHeavyChunk, g->heavy, H, C, &g->h_hv, &g->h_hfirst, s));
+    g->heavy_C = C;
+    g->heavy_H = H;
+    return NK_OK;
+}
+
+int heavy_view(nk_graph *g, int chunk, cudaStream_t s, HeavyView *out)
+{
+    if (chunk <= 0 || chunk == kHeavyChunk) {
+        NK_TRY(build_heavy(g, s));
+        *out = {g->heavy[0].as<int32_t>(), g->heavy[1].as<int32_t>(), g->heavy[2].as<int32_t>(),
+                g->heavy_H, g->heavy_C, kHeavyChunk};
+        return NK_OK;
+    }
+    std::lock_guard<std::mutex> lk(g->heavy_mu);
+    if (g->heavy_alt_H < 0 || g->heavy_alt_chunk != chunk) {
+        int32_t H = -1, C = 0;
+        g->heavy_alt_H = -1;
+        NK_TRY(build_table(g, chunk, g->heavy_alt, H, C, nullptr, nullptr, s));
+        g->heavy_alt_H = H;
+        g->heavy_alt_C = C;
+        g->heavy_alt_chunk = chunk;
+    }
+    *out = {g->heavy_alt[0].as<int32_t>(), g->heavy_alt[1].as<int32_t>(), g->heavy_alt[2].as<int32_t>(),
+            g->heavy_alt_H, g->heavy_alt_C, chunk};
     return NK_OK;
 }
 

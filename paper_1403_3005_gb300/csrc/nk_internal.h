@@ -88,7 +88,7 @@ struct CapturedRun {
     bool valid = false;
     uint64_t seed = 0;
     int32_t k = 0;
-    int batch = 0, dir = 0, grid_ctas = 0;
+    int batch = 0, dir = 0, grid_ctas = 0, chunk = 0;
     double alpha = 0, scale = 0;
     double *scores = nullptr;
     DevBuf ws[8];
@@ -114,6 +114,7 @@ struct Tuned {
     int batch = 64;
     double alpha = 1.0;
     int tpv = 8;
+    int chunk = 0;  // arcs per hub chunk of the batched sweep (0: kHeavyChunk)
 };
 
 }  // namespace nk
@@ -137,6 +138,9 @@ struct nk_graph {
     std::vector<int32_t> h_hv, h_hfirst;  // host copies of heavy[0] and heavy[1]
     nk::CapturedRun captured;             // last call captured with NK_RUN_CUDA_GRAPH
     int32_t vd_est = -1;                  // cached vertex-diameter bound (nk_rk.cu), -1 = not yet
+    // a second chunk table with another chunk size, for the batched sweep only (built on demand)
+    nk::DevBuf heavy_alt[3];
+    int32_t heavy_alt_H = -1, heavy_alt_C = 0, heavy_alt_chunk = 0;
     nk::DevBuf wt;                        // int32[A] arc weights (nk_weighted.cu), when weighted
     bool weighted = false;
 };
@@ -171,6 +175,13 @@ int scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t count, int64_t *
 constexpr int kHeavyChunk = 256;
 // Builds g->heavy (vertex ids, first chunk per vertex, owner per chunk) once per graph.
 int build_heavy(nk_graph *g, cudaStream_t s);
+// The chunk table for `chunk` arcs per chunk (0 or kHeavyChunk: the graph's own table, else a
+// second table kept for the last other size asked for).
+struct HeavyView {
+    const int32_t *hv, *hfirst, *chunk_h;
+    int32_t H, C, chunk;
+};
+int heavy_view(nk_graph *g, int chunk, cudaStream_t s, HeavyView *out);
 
 // ---------------------------------------------------------------- CSR build (nk_graph.cu)
 // Canonical CSR of the undirected edge list (u[i], v[i]) (device arrays), written into
@@ -198,6 +209,7 @@ struct RunCfg {
     unsigned long long *far = nullptr;    // closeness distance sums (device), or null
     unsigned long long *reach = nullptr;  // closeness reach counts (device), or null
     double *edge = nullptr;               // edge betweenness: per-arc sums (device, A), or null
+    int chunk = 0;                        // batched sweep: arcs per hub chunk (0: kHeavyChunk)
     // error-bounded estimate: per source index i, the target of its random shortest path,
     // the key of the walk's random stream, and the per-vertex counts of interior vertices
     const int32_t *rk_t = nullptr;

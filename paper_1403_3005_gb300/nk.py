@@ -41,7 +41,8 @@ class NkError(RuntimeError):
 class RunOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("batch", ctypes.c_int32), ("tpv", ctypes.c_int32),
                 ("direction", ctypes.c_int32), ("alpha", ctypes.c_double),
-                ("flags", ctypes.c_uint32), ("grid_ctas", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("flags", ctypes.c_uint32), ("grid_ctas", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class RunStats(ctypes.Structure):
@@ -282,10 +283,11 @@ def sssp_noalloc(row_ptr, col, s: int, dist, sigma, stream=None) -> None:
 
 
 # ---------------------------------------------------------------- betweenness
-def run_opts(mode=MODE_AUTO, batch=0, tpv=0, direction=DIR_AUTO, alpha=0.0, flags=0, grid_ctas=0) -> RunOpts:
+def run_opts(mode=MODE_AUTO, batch=0, tpv=0, direction=DIR_AUTO, alpha=0.0, flags=0, grid_ctas=0,
+             chunk=0) -> RunOpts:
     o = RunOpts()
     o.mode, o.batch, o.tpv, o.direction, o.alpha, o.flags = mode, batch, tpv, direction, alpha, flags
-    o.grid_ctas = grid_ctas
+    o.grid_ctas, o.chunk = grid_ctas, chunk
     return o
 
 

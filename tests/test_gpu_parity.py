@@ -46,6 +46,7 @@ MODES = [
     dict(mode=2, batch=64), dict(mode=2, batch=128), dict(mode=2, batch=256),
     dict(mode=2, batch=64, direction=1), dict(mode=2, batch=64, direction=2),
     dict(mode=2, batch=128, alpha=0.05), dict(mode=2, batch=64, alpha=50.0),
+    dict(mode=2, batch=128, chunk=64), dict(mode=2, batch=64, direction=2, chunk=32),
 ]
 
 SMALL = {
@@ -555,3 +556,18 @@ def test_grid_ctas_option_parity_and_determinism(nk):
     with pytest.raises(nk.NkError) as e:
         nk.betweenness_sampled(g, 3, 300, nk.run_opts(grid_ctas=-1))
     assert e.value.rc == nk.ERR_ARG
+
+
+def test_chunk_option(nk):
+    g, rp, col = both(nk, SMALL["hubs"])
+    want = oracle.betweenness_sampled(rp, col, 4, 500)
+    for chunk in (32, 96, 128, 512, 4096):
+        for B in (64, 256):
+            assert close(nk.betweenness_sampled(g, 4, 500, nk.run_opts(mode=2, batch=B, chunk=chunk)), want), (chunk, B)
+    for bad in (-32, 16, 100, 8192):
+        with pytest.raises(nk.NkError) as e:
+            nk.betweenness_sampled(g, 4, 500, nk.run_opts(mode=2, chunk=bad))
+        assert e.value.rc == nk.ERR_ARG
+    opts = nk.autotune(g, 4, 500)
+    assert opts.chunk in (0, 128)
+    assert close(nk.betweenness_sampled(g, 4, 500, opts), want)
