@@ -262,6 +262,22 @@ def serving_load(nk, torch, n_req, seed=3):
             "closed_loop_launches": cst["jobs"], "closed_loop_packed_requests": cst["packed_requests"]}
 
 
+def host_info():
+    """Cores and CPU model of the host the oracle runs on."""
+    import platform
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "machine": platform.machine(), "cpu": model}
+
+
 def cpu_baseline(cfg, seconds, rank_seed):
     """The oracle, as it stands, on one host core: Brandes on the first sources of the
     same sampled set of the oracle's own copy of the graph, until `seconds` pass."""
@@ -283,7 +299,8 @@ def cpu_baseline(cfg, seconds, rank_seed):
     t = time.perf_counter() - t0
     return {"value": m * done / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{done} of the {len(src)} sources of the same workload, "
-                      f"oracle-generated graph, {t:.1f} s on 1 host core"}
+                      f"oracle-generated graph, {t:.1f} s on 1 host core",
+            "host": host_info()}
 
 
 # ------------------------------------------------------------------ widened rows
@@ -485,7 +502,8 @@ def run_reference(args, world, rank):
             "config": {"workload": cfg["workload"], "n": n, "m": m, "k": cfg["k"],
                        "sources_per_step": per_step},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{per_step} sources per step of the {len(src)}-source workload"},
+                             "sample": f"{per_step} sources per step of the {len(src)}-source workload",
+                             "host": host_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
