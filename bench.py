@@ -594,7 +594,8 @@ def run_ours(args, world, rank, local):
            "dtype": "f64", "data": "synthetic",
            "config": {"workload": cfg["workload"], "n": n, "m": m, "arcs": A, "k": k,
                       "graph_seed": GRAPH_SEED, "sample_seed": sseed, "form": "batched",
-                      "batch": B, "alpha": stats["alpha"], "max_depth": stats["max_depth"],
+                      "batch": B, "alpha": stats["alpha"], "chunk": int(opts.chunk) or 256,
+                      "max_depth": stats["max_depth"],
                       "td_levels": stats["td_levels"], "bu_levels": stats["bu_levels"],
                       "l2": "flushed (256 MiB write) between steps", "sigma": "uint64",
                       "parallelism": f"sources split over {world} GPU(s), no collective"},
