@@ -140,6 +140,9 @@ int nk_sssp_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col, int64
 
 #define NK_RUN_DEVICE_PTRS 1u  /* scores (and src) are device pointers */
 #define NK_RUN_TIME_KERNELS 2u /* record per-launch durations of the sweep kernel */
+#define NK_RUN_RELABEL 8u      /* batched betweenness on a relabelled copy of the graph (vertex
+                                  v becomes v * 2654435761 mod n; results mapped back) */
+#define NK_RUN_NO_RELABEL 16u  /* never relabel (without either flag: the autotuner's choice) */
 #define NK_RUN_CUDA_GRAPH 4u   /* sampled, batched, device pointers: capture the whole call
                                   (sampler, persistent launches, scaling) into a CUDA graph
                                   on first use and replay it for later calls with the same

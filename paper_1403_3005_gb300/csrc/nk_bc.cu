@@ -30,6 +30,22 @@ __global__ void k_check_src(const int32_t *src, int32_t k, int32_t n, int *bad)
         if ((unsigned)src[i] >= (unsigned)n) atomicOr(bad, 1);
 }
 
+// ids of the relabelled copy: out[i] = perm[in[i]]
+__global__ void k_map_ids(const int32_t *perm, const int32_t *in, int32_t k, int32_t *out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = perm[in[i]];
+}
+
+// scores back to the caller's ids: out[v] = in[perm[v]]
+__global__ void k_gather_scores(const int32_t *perm, const double *in, int32_t n, double *out)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        out[v] = in[perm[v]];
+}
+
+int grid_of(int64_t items) { return (int)std::max<int64_t>(1, std::min<int64_t>((items + 255) / 256, 8LL * num_sms())); }
+
 RunCfg cfg_of(const nk_run_opts *o, const nk_graph *g)
 {
     RunCfg c;
@@ -45,6 +61,8 @@ RunCfg cfg_of(const nk_run_opts *o, const nk_graph *g)
     }
     if (c.alpha <= 0 && g->tuned.valid) c.alpha = g->tuned.alpha;
     if (c.chunk == 0 && g->tuned.valid) c.chunk = g->tuned.chunk;
+    const uint32_t fl = o ? o->flags : 0u;
+    c.relabel = (fl & NK_RUN_RELABEL) ? true : (fl & NK_RUN_NO_RELABEL) ? false : (g->tuned.valid && g->tuned.relabel);
     return c;
 }
 
@@ -65,6 +83,24 @@ int check_cfg(const RunCfg &c)
 int run_device(nk_graph *g, const int32_t *d_src, int32_t k, double scale, double *d_scores,
                const RunCfg &cfg, cudaStream_t s)
 {
+    const bool batched = cfg.mode == NK_MODE_BATCHED || (cfg.mode == NK_MODE_AUTO && k >= 16);
+    if (cfg.relabel && batched && !cfg.ws && build_relabeled(g, s) == NK_OK) {
+        // the same sweep on the relabelled copy: sources mapped in, scores gathered back
+        Tmp msrc, isc;
+        NK_TRY(msrc.alloc(sizeof(int32_t) * (size_t)k, s));
+        NK_TRY(isc.alloc(sizeof(double) * (size_t)g->n, s));
+        const int32_t *perm = g->relab_perm.as<int32_t>();
+        k_map_ids<<<grid_of(k), 256, 0, s>>>(perm, d_src, k, msrc.as<int32_t>());
+        ::nk::count_launch();
+        RunCfg c2 = cfg;
+        c2.relabel = false;
+        if (c2.batch == 0 && g->tuned.valid) c2.batch = g->tuned.batch;  // the copy is not tuned itself
+        NK_TRY(run_device(g->relab.get(), msrc.as<int32_t>(), k, scale, isc.as<double>(), c2, s));
+        k_gather_scores<<<grid_of(g->n), 256, 0, s>>>(perm, isc.as<double>(), g->n, d_scores);
+        ::nk::count_launch();
+        NK_CUDA(cudaGetLastError());
+        return NK_OK;
+    }
     NK_CUDA(cudaMemsetAsync(d_scores, 0, sizeof(double) * g->n, s));
     t_stats = RunStats();
     int mode = cfg.mode;
@@ -103,15 +139,25 @@ int run_captured(nk_graph *g, uint64_t seed, int32_t k, double scale, double *d_
     if (cfg.batch == 0) cfg.batch = g->tuned.valid ? g->tuned.batch : 64;
     if (cfg.alpha <= 0) cfg.alpha = 1.0;
     cfg.ws = e.ws;
+    if (cfg.relabel && build_relabeled(g, s) != NK_OK) cfg.relabel = false;
+    // with relabelling the sweep runs on the copy: sources mapped in, scores gathered back
+    nk_graph *gr = cfg.relabel ? g->relab.get() : g;
     const bool hit = e.valid && e.seed == seed && e.k == k && e.batch == cfg.batch &&
                      e.alpha == cfg.alpha && e.dir == cfg.direction && e.scores == d_scores &&
-                     e.scale == scale && e.grid_ctas == cfg.grid_ctas && e.chunk == cfg.chunk;
+                     e.scale == scale && e.grid_ctas == cfg.grid_ctas && e.chunk == cfg.chunk &&
+                     e.relabel == cfg.relabel;
     if (!hit) {
         e.reset();
         NK_TRY(e.src.ensure(sizeof(int32_t) * k));
+        if (cfg.relabel) {
+            NK_TRY(e.msrc.ensure(sizeof(int32_t) * k));
+            NK_TRY(e.iscores.ensure(sizeof(double) * (size_t)g->n));
+        }
+        int32_t *sweep_src = cfg.relabel ? e.msrc.as<int32_t>() : e.src.as<int32_t>();
+        double *sweep_scores = cfg.relabel ? e.iscores.as<double>() : d_scores;
         Ctrl *ctrls = nullptr;
         int nb = 0;
-        NK_TRY(enqueue_batched(g, e.src.as<int32_t>(), k, d_scores, cfg, s, true, &ctrls, &nb));
+        NK_TRY(enqueue_batched(gr, sweep_src, k, sweep_scores, cfg, s, true, &ctrls, &nb));
         const int nbatch = (k + cfg.batch - 1) / cfg.batch;
         NK_CUDA(cudaMallocHost(&e.h_status, sizeof(Ctrl) * nbatch));
         NK_CUDA(cudaStreamSynchronize(s));
@@ -120,10 +166,18 @@ int run_captured(nk_graph *g, uint64_t seed, int32_t k, double scale, double *d_
         NK_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         int rc = NK_OK;
         do {
-            if (cudaMemsetAsync(d_scores, 0, sizeof(double) * g->n, s) != cudaSuccess) { rc = set_error(NK_ERR_CUDA, "memset in capture"); break; }
+            if (cudaMemsetAsync(sweep_scores, 0, sizeof(double) * g->n, s) != cudaSuccess) { rc = set_error(NK_ERR_CUDA, "memset in capture"); break; }
             if ((rc = sample_sources_device(g->n, seed, k, e.src.as<int32_t>(), s)) != NK_OK) break;
-            if ((rc = enqueue_batched(g, e.src.as<int32_t>(), k, d_scores, cfg, s, false, &ctrls, &nb)) != NK_OK) break;
-            if ((rc = scale_vector(d_scores, g->n, scale, s)) != NK_OK) break;
+            if (cfg.relabel) {
+                k_map_ids<<<grid_of(k), 256, 0, s>>>(g->relab_perm.as<int32_t>(), e.src.as<int32_t>(), k, sweep_src);
+                ::nk::count_launch();
+            }
+            if ((rc = enqueue_batched(gr, sweep_src, k, sweep_scores, cfg, s, false, &ctrls, &nb)) != NK_OK) break;
+            if ((rc = scale_vector(sweep_scores, g->n, scale, s)) != NK_OK) break;
+            if (cfg.relabel) {
+                k_gather_scores<<<grid_of(g->n), 256, 0, s>>>(g->relab_perm.as<int32_t>(), sweep_scores, g->n, d_scores);
+                ::nk::count_launch();
+            }
             if (cudaMemcpyAsync(e.h_status, ctrls, sizeof(Ctrl) * nb, cudaMemcpyDeviceToHost, s) != cudaSuccess) { rc = set_error(NK_ERR_CUDA, "status copy in capture"); break; }
         } while (false);
         const cudaError_t ce = cudaStreamEndCapture(s, &graph);
@@ -150,6 +204,7 @@ int run_captured(nk_graph *g, uint64_t seed, int32_t k, double scale, double *d_
         e.scale = scale;
         e.grid_ctas = cfg.grid_ctas;
         e.chunk = cfg.chunk;
+        e.relabel = cfg.relabel;
         e.nb = nb;
         e.launches = captured;
     }
@@ -706,6 +761,8 @@ int nk_autotune(const nk_graph *gc, uint64_t seed, int32_t k, nk_run_opts *best)
     NK_TRY(dsrc.alloc(sizeof(int32_t) * k, s));
     NK_TRY(dsc.alloc(sizeof(double) * g->n, s));
     NK_TRY(sample_sources_device(g->n, seed, k, dsrc.as<int32_t>(), s));
+    nk_graph *tg = g;                      // the graph trials run on
+    const int32_t *tsrc = dsrc.as<int32_t>();
     auto trial = [&](int B, double alpha, double *ms_per_src, int chunk = 0) -> int {
         RunCfg c;
         c.mode = NK_MODE_BATCHED;
@@ -716,9 +773,9 @@ int nk_autotune(const nk_graph *gc, uint64_t seed, int32_t k, nk_run_opts *best)
         const int32_t kk = std::min<int32_t>(ks, B);
         NK_CUDA(cudaMemsetAsync(dsc.p, 0, sizeof(double) * g->n, s));
         RunStats st;
-        NK_TRY(run_batched(g, dsrc.as<int32_t>(), kk, dsc.as<double>(), c, &st, s));  // warm
+        NK_TRY(run_batched(tg, tsrc, kk, dsc.as<double>(), c, &st, s));  // warm
         st = RunStats();
-        NK_TRY(run_batched(g, dsrc.as<int32_t>(), kk, dsc.as<double>(), c, &st, s));
+        NK_TRY(run_batched(tg, tsrc, kk, dsc.as<double>(), c, &st, s));
         *ms_per_src = st.kernel_ms / kk;
         return NK_OK;
     };
@@ -754,15 +811,38 @@ int nk_autotune(const nk_graph *gc, uint64_t seed, int32_t k, nk_run_opts *best)
             bestC = 128;
         }
     }
+    // the relabelled copy, where bottom-up levels often pay off
+    bool bestR = false;
+    if (build_relabeled(g, s) == NK_OK) {
+        Tmp msrc;
+        NK_TRY(msrc.alloc(sizeof(int32_t) * (size_t)k, s));
+        k_map_ids<<<grid_of(k), 256, 0, s>>>(g->relab_perm.as<int32_t>(), dsrc.as<int32_t>(), k, msrc.as<int32_t>());
+        ::nk::count_launch();
+        tg = g->relab.get();
+        tsrc = msrc.as<int32_t>();
+        for (double alpha : {0.25, 4.0, 16.0}) {
+            double t;
+            NK_TRY(trial(bestB, alpha, &t, bestC));
+            if (t < bestT) {
+                bestT = t;
+                bestA = alpha;
+                bestR = true;
+            }
+        }
+        tg = g;
+        tsrc = dsrc.as<int32_t>();
+    }
     g->tuned.valid = true;
     g->tuned.batch = bestB;
     g->tuned.alpha = bestA;
     g->tuned.chunk = bestC;
+    g->tuned.relabel = bestR;
     *best = nk_run_opts();
     best->mode = NK_MODE_BATCHED;
     best->batch = bestB;
     best->alpha = bestA;
     best->chunk = bestC;
+    best->flags = bestR ? NK_RUN_RELABEL : NK_RUN_NO_RELABEL;
     return NK_OK;
 }
 

@@ -532,6 +532,51 @@ int heavy_view(nk_graph *g, int chunk, cudaStream_t s, HeavyView *out)
     return NK_OK;
 }
 
+__global__ void k_relabel_perm(int32_t n, int32_t *perm)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        perm[v] = (int32_t)(((unsigned long long)v * kRelabelMul) % (unsigned long long)n);
+}
+
+__global__ void k_relabel_arcs(const int32_t *rp, const int32_t *col, int32_t n, const int32_t *perm,
+                               int32_t *eu, int32_t *ev)
+{
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t pu = perm[u];
+        for (int32_t j = rp[u]; j < rp[u + 1]; ++j) {
+            eu[j] = pu;
+            ev[j] = perm[col[j]];
+        }
+    }
+}
+
+// The relabelled copy: the arcs (perm[u], perm[v]) through the canonical CSR builder.
+int build_relabeled(nk_graph *g, cudaStream_t s)
+{
+    if (g->relab) return NK_OK;
+    if (2 * g->A >= (int64_t)INT_MAX) return set_error(NK_ERR_NOMEM, "graph too large to relabel");
+    const int32_t n = g->n;
+    NK_TRY(g->relab_perm.ensure(sizeof(int32_t) * (size_t)n));
+    k_relabel_perm<<<grid_for(n, 256), 256, 0, s>>>(n, g->relab_perm.as<int32_t>());
+    ::nk::count_launch();
+    Tmp eu, ev;
+    NK_TRY(eu.alloc(sizeof(int32_t) * (size_t)std::max<int64_t>(g->A, 1), s));
+    NK_TRY(ev.alloc(sizeof(int32_t) * (size_t)std::max<int64_t>(g->A, 1), s));
+    k_relabel_arcs<<<grid_for(n, 256), 256, 0, s>>>(g->rp.as<int32_t>(), g->col.as<int32_t>(), n,
+                                                     g->relab_perm.as<int32_t>(), eu.as<int32_t>(), ev.as<int32_t>());
+    ::nk::count_launch();
+    NK_CUDA(cudaGetLastError());
+    nk_graph *r = new (std::nothrow) nk_graph();
+    if (!r) return set_error(NK_ERR_NOMEM, "host allocation failed");
+    const int rc = build_csr_from_edges(r, n, g->A, eu.as<int32_t>(), ev.as<int32_t>(), s);
+    if (rc != NK_OK) {
+        delete r;
+        return rc;
+    }
+    g->relab.reset(r);
+    return NK_OK;
+}
+
 }  // namespace nk
 
 using namespace nk;

@@ -7,6 +7,7 @@
 #include <atomic>
 #include <cstdarg>
 #include <cstdint>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -89,10 +90,11 @@ struct CapturedRun {
     uint64_t seed = 0;
     int32_t k = 0;
     int batch = 0, dir = 0, grid_ctas = 0, chunk = 0;
+    bool relabel = false;
     double alpha = 0, scale = 0;
     double *scores = nullptr;
     DevBuf ws[8];
-    DevBuf src;
+    DevBuf src, msrc, iscores;  // sources; relabelled sources and scores (relabel only)
     Ctrl *h_status = nullptr;  // pinned copy of the per-batch status words
     int nb = 0;
     uint64_t launches = 0;     // kernels one replay runs
@@ -115,6 +117,7 @@ struct Tuned {
     double alpha = 1.0;
     int tpv = 8;
     int chunk = 0;  // arcs per hub chunk of the batched sweep (0: kHeavyChunk)
+    bool relabel = false;  // batched betweenness on the relabelled copy
 };
 
 }  // namespace nk
@@ -143,6 +146,10 @@ struct nk_graph {
     int32_t heavy_alt_H = -1, heavy_alt_C = 0, heavy_alt_chunk = 0;
     nk::DevBuf wt;                        // int32[A] arc weights (nk_weighted.cu), when weighted
     bool weighted = false;
+    // relabelled copy for the batched sweep (vertex v of this graph is vertex relab_perm[v] of
+    // the copy), built on first use
+    std::unique_ptr<nk_graph> relab;
+    nk::DevBuf relab_perm;
 };
 
 namespace nk {
@@ -182,6 +189,12 @@ struct HeavyView {
     int32_t H, C, chunk;
 };
 int heavy_view(nk_graph *g, int chunk, cudaStream_t s, HeavyView *out);
+// Relabelling for the batched sweep: vertex v becomes (v * kRelabelMul) mod n, a bijection
+// (kRelabelMul is a prime above 2^31, so it has no factor in common with n).  Vertex ids of
+// power-law generators cluster the hubs at small ids; scattered ids spread them over the
+// scan windows of the sweep's levels.
+constexpr unsigned long long kRelabelMul = 2654435761ull;
+int build_relabeled(nk_graph *g, cudaStream_t s);
 
 // ---------------------------------------------------------------- CSR build (nk_graph.cu)
 // Canonical CSR of the undirected edge list (u[i], v[i]) (device arrays), written into
@@ -210,6 +223,7 @@ struct RunCfg {
     unsigned long long *reach = nullptr;  // closeness reach counts (device), or null
     double *edge = nullptr;               // edge betweenness: per-arc sums (device, A), or null
     int chunk = 0;                        // batched sweep: arcs per hub chunk (0: kHeavyChunk)
+    bool relabel = false;                 // betweenness entry: use the relabelled copy
     // error-bounded estimate: per source index i, the target of its random shortest path,
     // the key of the walk's random stream, and the per-vertex counts of interior vertices
     const int32_t *rk_t = nullptr;

@@ -25,7 +25,7 @@ CSR_VALIDATE, CSR_CANONICALISE, CSR_DEVICE_PTRS = 1, 2, 4
 GEN_ER, GEN_BA, GEN_RMAT = 1, 2, 3
 MODE_AUTO, MODE_PER_SOURCE, MODE_BATCHED = 0, 1, 2
 DIR_AUTO, DIR_TOP_DOWN, DIR_BOTTOM_UP = 0, 1, 2
-RUN_DEVICE_PTRS, RUN_TIME_KERNELS, RUN_CUDA_GRAPH = 1, 2, 4
+RUN_DEVICE_PTRS, RUN_TIME_KERNELS, RUN_CUDA_GRAPH, RUN_RELABEL, RUN_NO_RELABEL = 1, 2, 4, 8, 16
 
 _NAMES = {OK: "NK_OK", PENDING: "NK_PENDING", ERR_ARG: "NK_ERR_ARG", ERR_GRAPH: "NK_ERR_GRAPH",
           ERR_NOMEM: "NK_ERR_NOMEM", ERR_OVERFLOW: "NK_ERR_OVERFLOW", ERR_CUDA: "NK_ERR_CUDA",

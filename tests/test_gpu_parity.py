@@ -571,3 +571,33 @@ def test_chunk_option(nk):
     opts = nk.autotune(g, 4, 500)
     assert opts.chunk in (0, 128)
     assert close(nk.betweenness_sampled(g, 4, 500, opts), want)
+
+
+# ------------------------------------------------------------------ relabelled copy of the graph
+@pytest.mark.parametrize("name", ["hubs", "components", "grid", "star_big", "path"])
+def test_relabel_parity(nk, name):
+    g, rp, col = both(nk, SMALL[name])
+    n = len(rp) - 1
+    want = oracle.betweenness_exact(rp, col)
+    for m in (dict(mode=2, batch=64), dict(mode=2, batch=128, direction=2), dict(mode=2, batch=256, chunk=64)):
+        got = nk.betweenness_sources(g, np.arange(n, dtype=np.int32), 0.5, nk.run_opts(flags=nk.RUN_RELABEL, **m))
+        assert close(got, want), (name, m)
+
+
+def test_relabel_sampled_device_graph_and_autotune(nk):
+    import torch
+    g = nk.graph_generate("rmat", 14, 3)
+    n, rp, col = oracle.generate("rmat", 14, 3)
+    want = oracle.betweenness_sampled(rp, col, 5, 300)
+    o = nk.run_opts(mode=2, batch=128, alpha=16.0, flags=nk.RUN_RELABEL)
+    assert close(nk.betweenness_sampled(g, 5, 300, o), want)
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    go = nk.run_opts(mode=2, batch=128, alpha=16.0, flags=nk.RUN_RELABEL | nk.RUN_CUDA_GRAPH)
+    for _ in range(2):                                  # capture, then replay
+        out.fill_(-1.0)
+        nk.betweenness_sampled(g, 5, 300, go, out=out)
+        assert close(out.cpu().numpy(), want)
+    opts = nk.autotune(g, 5, 300)
+    assert opts.flags & (nk.RUN_RELABEL | nk.RUN_NO_RELABEL)
+    assert close(nk.betweenness_sampled(g, 5, 300, opts), want)
+    assert close(nk.betweenness_sampled(g, 5, 300), want)   # the tuned choice, no options
