@@ -65,6 +65,7 @@ def parse():
     p.add_argument("--no-ext", action="store_true", help="skip the closeness / edge / estimate / weighted legs")
     p.add_argument("--batch", type=int, default=0)
     p.add_argument("--relabel", action="store_true", help="with --batch: run on the relabelled copy")
+    p.add_argument("--alpha", type=float, default=0.0, help="with --batch: the top-down/bottom-up switch")
     return p.parse_args()
 
 
@@ -539,7 +540,8 @@ def run_ours(args, world, rank, local):
         src_dev = torch.arange(n, dtype=torch.int32, device="cuda")
     else:
         opts = nk.autotune(g, sseed, k) if not args.batch else nk.run_opts(
-            mode=nk.MODE_BATCHED, batch=args.batch, flags=nk.RUN_RELABEL if args.relabel else nk.RUN_NO_RELABEL)
+            mode=nk.MODE_BATCHED, batch=args.batch, alpha=args.alpha,
+            flags=nk.RUN_RELABEL if args.relabel else nk.RUN_NO_RELABEL)
         src_dev = None
     opts.flags |= nk.RUN_TIME_KERNELS
     scores = torch.empty(n, dtype=torch.float64, device="cuda")
