@@ -198,9 +198,12 @@ int nk_betweenness_sources(const nk_graph *g, const int32_t *src, int32_t k, dou
 /* Stats of the calling thread's last betweenness call. */
 int nk_last_run_stats(nk_run_stats *out);
 
-/* Autotuner: times candidate (batch, alpha, tpv) settings on a short sample of the
- * graph's own sources and writes the fastest into *best (cached per graph; later
- * calls with batch/alpha = 0 use it). */
+/* Autotuner: on one launch of up to 256 of the run's own sources (seed, k), times the
+ * batched sweep with 64/128/256 sources per launch, then alpha in {0.25, 1, 4, 16}, then hub
+ * chunks of 128 arcs against 256, then the relabelled copy (NK_RUN_RELABEL) with alpha in
+ * {0.25, 4, 16}; writes the fastest into *best (flags: NK_RUN_RELABEL or NK_RUN_NO_RELABEL).
+ * The choice is cached on the graph: later calls with batch/alpha/chunk = 0 and neither
+ * relabel flag use it.  Errors: NK_ERR_ARG (null pointers, k outside [1, n]). */
 int nk_autotune(const nk_graph *g, uint64_t seed, int32_t k, nk_run_opts *best);
 
 /* ---------------------------------------------------------------- weighted graphs (Sections 2.3, 3.4) */
