@@ -783,7 +783,7 @@ int nk_autotune(const nk_graph *gc, uint64_t seed, int32_t k, nk_run_opts *best)
     double bestA = 1.0, bestT = 1e30;
     for (int B : {64, 128, 256}) {
         if (B > 64 && ks < B / 2) break;
-        double t;
+        double t = 1e30;
         const int rc = trial(B, 1.0, &t);
         if (rc == NK_ERR_NOMEM) break;
         NK_TRY(rc);
@@ -793,7 +793,7 @@ int nk_autotune(const nk_graph *gc, uint64_t seed, int32_t k, nk_run_opts *best)
         }
     }
     for (double alpha : {0.25, 4.0, 16.0}) {
-        double t;
+        double t = 1e30;
         NK_TRY(trial(bestB, alpha, &t));
         if (t < bestT) {
             bestT = t;
@@ -804,7 +804,7 @@ int nk_autotune(const nk_graph *gc, uint64_t seed, int32_t k, nk_run_opts *best)
     // partial sums on others
     int bestC = 0;
     if (g->max_deg > 128) {
-        double t;
+        double t = 1e30;
         NK_TRY(trial(bestB, bestA, &t, 128));
         if (t < bestT) {
             bestT = t;
@@ -821,7 +821,7 @@ int nk_autotune(const nk_graph *gc, uint64_t seed, int32_t k, nk_run_opts *best)
         tg = g->relab.get();
         tsrc = msrc.as<int32_t>();
         for (double alpha : {0.25, 4.0, 16.0}) {
-            double t;
+            double t = 1e30;
             NK_TRY(trial(bestB, alpha, &t, bestC));
             if (t < bestT) {
                 bestT = t;
