@@ -84,14 +84,18 @@ int nk_graph_from_edges(int32_t n, int64_t m, const int32_t *u, const int32_t *v
 int nk_graph_generate(int kind, const double *params, int32_t n_or_scale, uint64_t seed,
                       nk_graph **out);
 
-/* n and the number of arcs A (= 2 * undirected edges). */
+/* n and the number of arcs A (= 2 * undirected edges) of the graph (Section 2.3: the
+ * graph data structure answers its node and edge counts). */
 int nk_graph_info(const nk_graph *g, int32_t *n, int64_t *n_arcs);
 
-/* Copies the canonical CSR to host arrays row_ptr[n+1] and col[A]. */
+/* Copies the canonical CSR to host arrays row_ptr[n+1] and col[A] (Section 2.3: the
+ * adjacency structure, here as the immutable int32 CSR the sweeps read).  Used to hand
+ * the same graph to another program, e.g. a checker. */
 int nk_graph_export_csr(const nk_graph *g, int32_t *row_ptr, int32_t *col);
 
-/* Frees the graph and its cached device workspace.  NK_ERR_ARG if serving requests on
- * it are still pending (the graph is then not freed). */
+/* Frees the graph and its cached device workspace (Section 2.3: the graph object owns
+ * its adjacency structure).  NK_ERR_ARG if serving requests on it are still pending (the
+ * graph is then not freed). */
 int nk_graph_free(nk_graph *g);
 
 /* ---------------------------------------------------------------- sampler (Section 3.2) */
@@ -119,10 +123,16 @@ int nk_sssp(const nk_graph *g, int32_t s, int32_t *dist, uint64_t *sigma);
  * Scratch (control words, BFS queue, per-level counters) is one static device array of
  * about 20 MiB that every GPU loading the library holds until the process exits, so
  * 1 <= n <= 1048576 (2^20); a larger n returns NK_ERR_ARG with a message.  The call makes
- * no cudaMalloc, cudaFree or other allocating call.  The first call on a device looks up
- * that device's address of the array (cudaGetSymbolAddress) with the device current:
- * make that first call before any stream capture.  All calls share the one array, so
- * calls that overlap on the GPU race: serialise them (one stream, or host ordering).
+ * no cudaMalloc, cudaFree or other allocating call (nk_alloc_count does not move).
+ * With CUDA's lazy module loading (the default), the array is reserved when the module
+ * that holds it first loads on a device: at the first call of this function or of
+ * another single-source sweep there.  Callers whose footprint must not grow after
+ * start-up therefore make one call at start-up.  That first call also looks up the
+ * device's address of the array (cudaGetSymbolAddress) with the device current.  The
+ * call copies the source id from pageable host memory and waits for its stream, so it
+ * must not be called on a stream that is being captured into a CUDA graph.  All calls
+ * share the one array, so calls that overlap on the GPU race: serialise them (one
+ * stream, or host ordering).
  * Rows are not split into chunks here, so hubs make it slower than nk_sssp.
  * Errors: NK_ERR_ARG, NK_ERR_OVERFLOW (sigma exceeded 2^64 - 1), NK_ERR_TIMEOUT,
  * NK_ERR_CUDA. */
@@ -195,10 +205,12 @@ int nk_betweenness_sampled_opts(const nk_graph *g, uint64_t seed, int32_t k, dou
 int nk_betweenness_sources(const nk_graph *g, const int32_t *src, int32_t k, double scale,
                            double *scores, const nk_run_opts *opts);
 
-/* Stats of the calling thread's last betweenness call. */
+/* Stats of the calling thread's last betweenness call (no counterpart in the paper:
+ * launch width, levels run top-down and bottom-up, kernel time). */
 int nk_last_run_stats(nk_run_stats *out);
 
-/* Autotuner: on one launch of up to 256 of the run's own sources (seed, k), times the
+/* Autotuner (no counterpart in the paper; it tunes the batched GPU sweep, which is this
+ * library's own design): on one launch of up to 256 of the run's own sources (seed, k), times the
  * batched sweep with 64/128/256 sources per launch, then alpha in {0.25, 1, 4, 16}, then hub
  * chunks of 128 arcs against 256, then the relabelled copy (NK_RUN_RELABEL) with alpha in
  * {0.25, 4, 16}; writes the fastest into *best (flags: NK_RUN_RELABEL or NK_RUN_NO_RELABEL).
@@ -312,11 +324,16 @@ typedef struct nk_server_stats {
     int64_t packed_requests;           /* requests that ran inside a packed launch */
 } nk_server_stats;
 
+/* Serving runtime: no counterpart in the paper.  The paper runs the sources of one
+ * betweenness computation in parallel (Section 3.2); the server extends that to many
+ * independent requests on different graphs, arriving over time, which run concurrently
+ * on the GPU (continuous batching with device-memory admission). */
 int nk_server_create(const nk_server_opts *opts, nk_server **out);
-/* Waits for pending requests, then frees the server. */
+/* Waits for pending requests, then frees the server (serving runtime, see above). */
 void nk_server_destroy(nk_server *srv);
 
-/* Queues a sampled-betweenness request (graph, seed, k).  `scores` (n doubles, host)
+/* Queues a sampled-betweenness request (graph, seed, k): the estimate of Section 3.2,
+ * computed as nk_betweenness_sampled computes it.  `scores` (n doubles, host)
  * must stay valid until nk_serve_poll returns something other than NK_PENDING.
  * Admission is by the device-memory budget; requests larger than the whole budget are
  * rejected with NK_ERR_NOMEM.  Consecutive small requests (graphs of up to 4M arcs,
@@ -326,29 +343,43 @@ void nk_server_destroy(nk_server *srv);
 int nk_serve_submit(nk_server *srv, const nk_graph *g, uint64_t seed, int32_t k,
                     double *scores, nk_req *id);
 
-/* NK_PENDING while queued or running; then NK_OK or the request's error code. */
+/* Serving runtime (no counterpart in the paper): NK_PENDING while queued or running;
+ * then NK_OK or the request's error code. */
 int nk_serve_poll(nk_server *srv, nk_req id);
 
-/* Blocks until request id is finished (or timeout_s elapses: NK_PENDING). */
+/* Serving runtime (no counterpart in the paper): blocks until request id is finished
+ * (or timeout_s elapses: NK_PENDING). */
 int nk_serve_wait(nk_server *srv, nk_req id, double timeout_s);
 
+/* Serving runtime (no counterpart in the paper): counters and latency percentiles. */
 int nk_server_get_stats(nk_server *srv, nk_server_stats *out);
 
 /* ---------------------------------------------------------------- misc */
-/* Stream used by every later call of this process (a cudaStream_t); NULL = default. */
+/* Stream used by every later call of this process (a cudaStream_t); NULL = default.
+ * No counterpart in the paper: CUDA stream plumbing, so that the calls are ordered with
+ * the caller's own GPU work (e.g. PyTorch's current stream). */
 int nk_set_stream(void *stream);
 
-/* Bound, in nanoseconds, on every device-side wait (grid barrier); default 10 s. */
+/* Bound, in nanoseconds, on every device-side wait (grid barrier); default 10 s.  No
+ * counterpart in the paper: failure detection around the persistent kernels. */
 int nk_set_wait_limit_ns(uint64_t ns);
 
-/* Failure-detection self test: launches a kernel whose wait on a flag that nothing
- * sets runs out after limit_ns; returns NK_ERR_TIMEOUT when the bounded wait works
+/* Failure-detection self test (no counterpart in the paper): launches a kernel whose
+ * wait on a flag that nothing sets runs out after limit_ns; returns NK_ERR_TIMEOUT when the bounded wait works
  * (and the CUDA context stays usable). */
 int nk_selftest_wait_timeout(uint64_t limit_ns);
 
-/* Number of kernels this library has launched in this process (all entry points). */
+/* Number of kernels this library has launched in this process (all entry points).  No
+ * counterpart in the paper: launch accounting. */
 uint64_t nk_launch_count(void);
 
+/* Number of memory allocation calls (cudaMalloc, cudaMallocAsync, cudaMallocHost) this
+ * library has made in this process (all entry points); a diagnostic, like the launch
+ * count, that shows which calls allocate. */
+uint64_t nk_alloc_count(void);
+
+/* Message of the calling thread's last failure; library version string.  No
+ * counterpart in the paper. */
 const char *nk_last_error(void);
 const char *nk_version(void);
 

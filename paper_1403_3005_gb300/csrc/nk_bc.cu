@@ -159,6 +159,7 @@ int run_captured(nk_graph *g, uint64_t seed, int32_t k, double scale, double *d_
         int nb = 0;
         NK_TRY(enqueue_batched(gr, sweep_src, k, sweep_scores, cfg, s, true, &ctrls, &nb));
         const int nbatch = (k + cfg.batch - 1) / cfg.batch;
+        ::nk::count_alloc();
         NK_CUDA(cudaMallocHost(&e.h_status, sizeof(Ctrl) * nbatch));
         NK_CUDA(cudaStreamSynchronize(s));
         const uint64_t l0 = g_launches.load();

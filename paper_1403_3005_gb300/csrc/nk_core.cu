@@ -30,6 +30,7 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line)
 }
 
 std::atomic<uint64_t> g_launches{0};
+std::atomic<uint64_t> g_allocs{0};
 
 // ---------------------------------------------------------------- stream / limits
 static std::atomic<cudaStream_t> g_stream{nullptr};
@@ -56,6 +57,7 @@ int DevBuf::ensure(size_t b)
     if (b <= bytes && p) return NK_OK;
     release();
     size_t want = b < 256 ? 256 : b;
+    count_alloc();
     cudaError_t e = stream_ordered ? cudaMallocAsync(&p, want, st) : cudaMalloc(&p, want);
     if (e != cudaSuccess) {
         p = nullptr;
@@ -80,6 +82,7 @@ void DevBuf::release()
 int Tmp::alloc(size_t b, cudaStream_t s)
 {
     st = s;
+    count_alloc();
     cudaError_t e = cudaMallocAsync(&p, b < 256 ? 256 : b, s);
     if (e != cudaSuccess) {
         p = nullptr;
@@ -252,6 +255,8 @@ const char *nk_last_error(void) { return t_err.c_str(); }
 const char *nk_version(void) { return "nk-gb300 0.1 (sm_103a)"; }
 
 uint64_t nk_launch_count(void) { return g_launches.load(); }
+
+uint64_t nk_alloc_count(void) { return g_allocs.load(); }
 
 int nk_set_stream(void *s)
 {

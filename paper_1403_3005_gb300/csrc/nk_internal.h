@@ -35,6 +35,10 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
 // Every kernel launch of the library bumps this process-wide counter.
 extern std::atomic<uint64_t> g_launches;
 inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+// Every memory allocation call of the library (cudaMalloc, cudaMallocAsync,
+// cudaMallocHost) bumps this process-wide counter.
+extern std::atomic<uint64_t> g_allocs;
+inline void count_alloc() { g_allocs.fetch_add(1, std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------- stream / limits
 cudaStream_t stream();

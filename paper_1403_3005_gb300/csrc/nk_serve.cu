@@ -126,6 +126,7 @@ int run_request(nk_server *S, Request *r, cudaStream_t st, double **h_buf, size_
         if (*h_buf) cudaFreeHost(*h_buf);
         *h_buf = nullptr;
         *h_cap = 0;
+        ::nk::count_alloc();
         NK_CUDA(cudaMallocHost(h_buf, sizeof(double) * n));
         *h_cap = n;
     }
@@ -266,6 +267,7 @@ int run_pack(nk_server *S, const std::vector<Request *> &rs, cudaStream_t st, do
         if (*h_buf) cudaFreeHost(*h_buf);
         *h_buf = nullptr;
         *h_cap = 0;
+        ::nk::count_alloc();
         NK_CUDA(cudaMallocHost(h_buf, sizeof(double) * n_u));
         *h_cap = n_u;
     }

@@ -511,7 +511,7 @@ int run(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores, const Ru
     const int tpv = cfg.tpv > 0 ? cfg.tpv : auto_tpv(g);
     Launch L;
     NK_TRY(pick_launch(tpv, L));
-    SrcArgs a;
+    SrcArgs a{};
     a.n = n;
     a.A = g->A;
     a.rp = g->rp.as<int32_t>();
@@ -682,7 +682,7 @@ extern "C" int nk_sssp_noalloc(int32_t n, const int32_t *row_ptr, const int32_t 
     const int tpv = avg <= 3 ? 2 : avg <= 12 ? 4 : avg <= 48 ? 8 : avg <= 160 ? 16 : 32;
     Launch L;
     NK_TRY(pick_launch(tpv, L));
-    SrcArgs a;
+    SrcArgs a{};
     a.n = n;
     a.A = n_arcs;
     a.rp = row_ptr;
@@ -704,6 +704,7 @@ extern "C" int nk_sssp_noalloc(int32_t n, const int32_t *row_ptr, const int32_t 
     a.H = 0;
     a.C = 0;
     a.part = reinterpret_cast<unsigned long long *>(scr + kNaPart);
+    a.edge = nullptr;
     // the control block keeps the previous call's words: it must start at zero
     NK_CUDA(cudaMemsetAsync(a.ctrl, 0, sizeof(Ctrl), st));
     NK_CUDA(cudaMemcpyAsync(scr + kNaSrc, &s, sizeof(int32_t), cudaMemcpyHostToDevice, st));

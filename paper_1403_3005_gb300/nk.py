@@ -118,6 +118,7 @@ SIGNATURES = {
     "nk_set_wait_limit_ns": (_INT, [_U64]),
     "nk_selftest_wait_timeout": (_INT, [_U64]),
     "nk_launch_count": (_U64, []),
+    "nk_alloc_count": (_U64, []),
     "nk_last_error": (ctypes.c_char_p, []),
     "nk_version": (ctypes.c_char_p, []),
 }
@@ -271,11 +272,40 @@ def sssp(g: Graph, s: int):
     return dist, sigma
 
 
+def _check_noalloc_buffers(row_ptr, col, dist, sigma):
+    """Refuses buffers the allocation-free sweep would read or write out of bounds, before
+    anything reaches the library: dtypes, sizes, contiguity, then that every tensor is a
+    CUDA tensor on the current device."""
+    import torch
+    for name, t, dt in (("row_ptr", row_ptr, torch.int32), ("col", col, torch.int32),
+                        ("dist", dist, torch.int32), ("sigma", sigma, torch.int64)):
+        if not _is_torch(t):
+            raise ValueError(f"{name} must be a torch tensor")
+        if t.dtype != dt:
+            raise ValueError(f"{name} must be {dt} (got {t.dtype})")
+        if t.dim() != 1 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous 1-D tensor")
+    n = row_ptr.numel() - 1
+    if n < 1:
+        raise ValueError("row_ptr needs n + 1 >= 2 entries")
+    if dist.numel() != n or sigma.numel() != n:
+        raise ValueError(f"dist and sigma need n = {n} entries (got {dist.numel()} and {sigma.numel()})")
+    for name, t in (("row_ptr", row_ptr), ("col", col), ("dist", dist), ("sigma", sigma)):
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+    cur = torch.cuda.current_device()
+    for name, t in (("row_ptr", row_ptr), ("col", col), ("dist", dist), ("sigma", sigma)):
+        if t.device.index != cur:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{cur}")
+    return n
+
+
 def sssp_noalloc(row_ptr, col, s: int, dist, sigma, stream=None) -> None:
     """Allocation-free forward sweep into caller-owned CUDA tensors: row_ptr (int32,
     n+1) and col (int32) hold a canonical CSR on the device; dist (int32, n) and sigma
-    (int64 storage read as uint64, n) receive the results.  See nk.h."""
-    n = row_ptr.numel() - 1
+    (int64 storage read as uint64, n) receive the results.  See nk.h.  Buffers of the
+    wrong type, size or device raise ValueError before any launch."""
+    n = _check_noalloc_buffers(row_ptr, col, dist, sigma)
     h = 0 if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
     _check(lib().nk_sssp_noalloc(n, _dev_ptr(row_ptr), _dev_ptr(col) if col.numel() else None,
                                  col.numel(), s, _dev_ptr(dist), _dev_ptr(sigma),
@@ -337,6 +367,56 @@ def betweenness_sources(g: Graph, src, scale: float, opts: RunOpts | None = None
     _check(lib().nk_betweenness_sources(g.handle, sp, k, scale, ptr,
                                          ctypes.byref(o) if o is not None else None))
     return res
+
+
+# ---------------------------------------------------------------- several GPUs (Section 3.2)
+def source_shard(src, rank: int, world: int):
+    """Contiguous slice `rank` of `world` of one source set: entries [k r / N, k (r+1) / N).
+    Sources are independent (Section 3.2), so the slices' dependency sums add up to the
+    whole set's."""
+    k = len(src)
+    return src[k * rank // world:k * (rank + 1) // world]
+
+
+def sharded_betweenness(n: int, src, rank: int, world: int, compute, group=None):
+    """One sampled estimate split over the ranks of a torch.distributed group: rank r
+    computes the unscaled dependency sums of its slice of the source set `src`
+    (compute(slice) -> float64 tensor of n entries, or None for an empty slice), one sum
+    all-reduce of the n-vector combines the ranks (the paper's per-thread arrays summed,
+    Section 3.2), and the sum is scaled by n / (2k).  Every rank returns the estimate."""
+    import torch
+    import torch.distributed as dist
+    part = source_shard(src, rank, world)
+    local = compute(part) if len(part) else None
+    if local is None:
+        dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend(group) == "nccl" else "cpu"
+        local = torch.zeros(n, dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(local, op=dist.ReduceOp.SUM, group=group)
+    local.mul_(n / (2.0 * len(src)))
+    return local
+
+
+def betweenness_sampled_sharded(g: Graph, seed: int, k: int, opts: RunOpts | None = None, group=None,
+                                out=None):
+    """nk_betweenness_sampled split over the GPUs of a torch.distributed (NCCL) group,
+    one GPU per rank, each holding its own copy of the graph: the k sources of
+    nk_sample_sources(n, seed, k) are sampled on every rank, rank r sweeps its contiguous
+    slice with nk_betweenness_sources (scale 1) into a device vector, one NCCL all-reduce
+    sums the n-vectors, and the sum is scaled by n / (2k).  Returns the estimate (a CUDA
+    tensor of n doubles) on every rank."""
+    import torch
+    import torch.distributed as dist
+    rank, world = dist.get_rank(group), dist.get_world_size(group)
+    n = g.n
+    dev = torch.device("cuda", torch.cuda.current_device())
+    src = sample_sources(n, seed, k, out=torch.empty(k, dtype=torch.int32, device=dev))
+    res = out if out is not None else torch.empty(n, dtype=torch.float64, device=dev)
+
+    def compute(part):
+        betweenness_sources(g, part, 1.0, opts, out=res)
+        return res
+    return sharded_betweenness(n, src, rank, world, compute, group)
 
 
 def set_weights(g: Graph, w) -> None:
@@ -535,6 +615,11 @@ def set_wait_limit_ns(ns: int) -> None:
 
 def selftest_wait_timeout(limit_ns: int) -> int:
     return lib().nk_selftest_wait_timeout(limit_ns)
+
+
+def alloc_count() -> int:
+    """Memory allocation calls the library has made in this process."""
+    return int(lib().nk_alloc_count())
 
 
 def launch_count() -> int:

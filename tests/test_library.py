@@ -75,26 +75,64 @@ def test_product_path_does_not_import_oracle():
                 assert "oracle" not in text.replace("oracle-free", ""), f
 
 
+def test_noalloc_refuses_bad_buffers_before_any_launch(libpath):
+    """The allocation-free sweep's binding checks dtype, size, contiguity and device of
+    every buffer before anything reaches the library (CPU tensors never get that far)."""
+    import torch
+    from paper_1403_3005_gb300 import nk
+    n = 10
+    rp = torch.zeros(n + 1, dtype=torch.int32)
+    col = torch.zeros(4, dtype=torch.int32)
+    dist = torch.zeros(n, dtype=torch.int32)
+    sigma = torch.zeros(n, dtype=torch.int64)
+    launches = nk.launch_count()
+    bad = [
+        ((rp.long(), col, dist, sigma), "row_ptr must be torch.int32"),
+        ((rp, col.long(), dist, sigma), "col must be torch.int32"),
+        ((rp, col, dist.long(), sigma), "dist must be torch.int32"),
+        ((rp, col, dist, sigma.int()), "sigma must be torch.int64"),
+        ((rp, col, dist[:n - 1], sigma), "need n = 10 entries"),
+        ((rp, col, dist, sigma[:n - 1]), "need n = 10 entries"),
+        ((rp, col, dist, torch.zeros(2 * n, dtype=torch.int64)[::2]), "contiguous"),
+        ((rp, col, dist, sigma), "must be a CUDA tensor"),
+        ((np.zeros(n + 1, np.int32), col, dist, sigma), "must be a torch tensor"),
+    ]
+    for args, msg in bad:
+        with pytest.raises(ValueError, match=msg):
+            nk.sssp_noalloc(args[0], args[1], 0, args[2], args[3])
+    assert nk.launch_count() == launches
+
+
 # ---------------------------------------------------------------- multi-rank sharding
+def test_source_shard_partitions_the_set():
+    from paper_1403_3005_gb300 import nk
+    for k in (1, 5, 8192, 8193):
+        src = np.arange(k)
+        for world in (1, 2, 3, 8):
+            parts = [nk.source_shard(src, r, world) for r in range(world)]
+            assert np.array_equal(np.concatenate(parts), src)
+            assert max(map(len, parts)) - min(map(len, parts)) <= 1
+
+
 def _shard_worker(rank, world, port, n, rp, col, src, q):
     import torch.distributed as dist
     import oracle
+    from paper_1403_3005_gb300 import nk
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     import torch
-    part = np.array_split(src, world)[rank]
-    local = oracle.betweenness_sources(rp, col, part, 1.0)
-    t = torch.from_numpy(local)
-    dist.all_reduce(t)
+    # the product's partition-and-reduce helper, with the oracle as the per-rank compute
+    got = nk.sharded_betweenness(n, src, rank, world,
+                                 lambda part: torch.from_numpy(oracle.betweenness_sources(rp, col, part, 1.0)))
     if rank == 0:
-        q.put(t.numpy() * (n / (2.0 * len(src))))
+        q.put(got.numpy())
     dist.barrier()
     dist.destroy_process_group()
 
 
 def test_source_sharding_over_two_gloo_ranks():
-    """Sources are independent (Section 3.2): a shard of the source set per rank and
-    one sum of the n-vector give the unsharded sampled estimate."""
+    """Sources are independent (Section 3.2): a contiguous slice of one source set per rank
+    and one sum all-reduce of the n-vector give the unsharded sampled estimate."""
     import multiprocessing as mp
     import socket
 
