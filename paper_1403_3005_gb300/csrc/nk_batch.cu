@@ -66,6 +66,10 @@ struct BArgs {
     const int32_t *rp, *col;
     const int32_t *src;
     int32_t nsrc;
+    // when set (captured calls), the number of sources of the whole run is *ksrc, read on
+    // the device, and this batch has min(B, *ksrc - boff) of them (none: it returns at once)
+    const int32_t *ksrc;
+    int32_t boff;
     int32_t lcap;                // levels 0..lcap may be non-empty; slabs 0..lcap+1
     unsigned long long *F;       // [lcap+2][n][W]
     unsigned long long *vis;     // [n][W]
@@ -150,17 +154,33 @@ template <int W> __device__ __forceinline__ Bits<W> andnot(const Bits<W> &x, con
 
 __device__ __forceinline__ int deg_of(const int32_t *rp, int v) { return __ldg(rp + v + 1) - __ldg(rp + v); }
 
-// Slot k of a lane covers source bit 32k + lane: word k/2, bit 32(k&1) + lane.
+// Source slots of a lane: lane L covers the adjacent source pairs {64q + 2L, 64q + 2L + 1}
+// of the batch's words q = 0..W-1, so that one 16-byte copy moves both of a pair's
+// values.  Slot k = 2q + e of lane L is source 64q + 2L + e: bit 2L + e of word q, and
+// entry 64q + 2L + e of a vertex's row of B values.
+__device__ __forceinline__ int slot_off(int k, int lane) { return 64 * (k >> 1) + 2 * lane + (k & 1); }
+
 template <int W> __device__ __forceinline__ bool has_slot(const Bits<W> &b, int k, int lane)
 {
-    return (b.w[k >> 1] >> (((k & 1) << 5) + lane)) & 1ull;
+    return (b.w[k >> 1] >> (2 * lane + (k & 1))) & 1ull;
 }
 
-// The same test on the 32-bit half-word that holds slot k, with lanebit = 1 << lane.
-template <int W> __device__ __forceinline__ bool slot_bit(const Bits<W> &b, int k, unsigned lanebit)
+// The two bits of lane L's pair in word q.
+template <int W> __device__ __forceinline__ unsigned pair_bits(unsigned long long word, int lane)
 {
-    const unsigned half = (k & 1) ? (unsigned)(b.w[k >> 1] >> 32) : (unsigned)b.w[k >> 1];
-    return (half & lanebit) != 0;
+    return (unsigned)(word >> (2 * lane)) & 3u;
+}
+
+// bit i of x moved to bit 2i
+__device__ __forceinline__ unsigned long long spread32(unsigned x)
+{
+    unsigned long long v = x;
+    v = (v | (v << 16)) & 0x0000FFFF0000FFFFull;
+    v = (v | (v << 8)) & 0x00FF00FF00FF00FFull;
+    v = (v | (v << 4)) & 0x0F0F0F0F0F0F0F0Full;
+    v = (v | (v << 2)) & 0x3333333333333333ull;
+    v = (v | (v << 1)) & 0x5555555555555555ull;
+    return v;
 }
 
 // acc += x with the carry out of bit 63 counted in carry (a path-count overflow).
@@ -179,11 +199,20 @@ __device__ __forceinline__ void check_failed(const BArgs &a, int code, int where
     }
 }
 
+// One warp's list of the relevant neighbours of the current 32-arc window of a gather:
+// their ids, masked source bits and arc indices, in shared memory.
+template <int W> struct Nbrs {
+    unsigned long long f[32][W];
+    int c[32];
+    int j[32];
+};
+
 // For the warp's vertex with adjacency [beg, end): per source slot, the sum of sp over
 // the neighbours c whose Fsel[c] & tgt holds that source bit; uint64 sums (sigma, with
-// carry detection) or double-single sums (psi).  Lanes over neighbours find the relevant
-// ones; then lanes over source bits read the contiguous sp rows, two neighbours per
-// round so that their loads are in flight together.
+// carry detection) or double-single sums (psi).  Lanes over arcs find the relevant
+// neighbours of a 32-arc window and list them in shared memory; then the lanes, each on
+// its source pairs, read two listed neighbours' rows per round with 16-byte loads (both
+// neighbours' loads in flight together) and add the relevant entries.
 // With EDGE (backward only) the warp's vertex v also hands every relevant arc (v, c) its
 // share sum_b sigma_b(v) * psi_b(c) over the gathered source bits (sv holds sigma_b(v) of
 // the lane's slots): a warp sum per neighbour, added to edge[j] by lane 0.  The arc is
@@ -192,11 +221,10 @@ template <int W, bool PSI, bool EDGE = false>
 __device__ __forceinline__ void gather(const BArgs &a, int beg, int end,
                                        const unsigned long long *Fsel, const Bits<W> &tgt,
                                        unsigned long long (&acc)[2 * W], dev::ff (&facc)[2 * W],
-                                       bool &ovf, const dev::ff *sv = nullptr)
+                                       bool &ovf, Nbrs<W> &st, const dev::ff *sv = nullptr)
 {
     constexpr int B = 64 * W;
     const int lane = threadIdx.x & 31;
-    const unsigned lanebit = 1u << lane;
     unsigned carry = 0;
     if (beg < 0 || end < beg || (long long)end > a.A) {  // warp-uniform
         if (lane == 0) check_failed(a, kErrCheck, 1, beg);
@@ -214,27 +242,39 @@ __device__ __forceinline__ void gather(const BArgs &a, int beg, int end,
 #pragma unroll
             for (int q = 0; q < W; ++q) f.w[q] = fc.w[q] & tgt.w[q];
         }
-        unsigned rel = __ballot_sync(FULL, any_bits<W>(f));
-        while (rel) {
-            const int s0 = __ffs(rel) - 1;
-            rel &= rel - 1;
-            int s1 = s0;
-            const bool two = rel != 0;
-            if (two) {
-                s1 = __ffs(rel) - 1;
-                rel &= rel - 1;
-            }
-            const int c0 = __shfl_sync(FULL, c, s0);
-            const int c1 = __shfl_sync(FULL, c, s1);
-            const Bits<W> f0 = shfl_bits<W>(f, s0);
-            const Bits<W> f1 = shfl_bits<W>(f, s1);
-            const unsigned long long *r0 = a.sp + (size_t)c0 * B + lane;
-            const unsigned long long *r1 = a.sp + (size_t)c1 * B + lane;
+        const bool mine = any_bits<W>(f);
+        const unsigned rel = __ballot_sync(FULL, mine);
+        if (!rel) continue;
+        if (mine) {
+            const int pos = __popc(rel & dev::lanemask_lt());
+            st.c[pos] = c;
+            st.j[pos] = j;
+#pragma unroll
+            for (int q = 0; q < W; ++q) st.f[pos][q] = f.w[q];
+        }
+        __syncwarp();
+        unsigned left = rel;
+        while (left) {
+            const int s0 = __ffs(left) - 1;
+            left &= left - 1;
+            const bool two = left != 0;
+            const int s1 = two ? __ffs(left) - 1 : s0;
+            if (two) left &= left - 1;
+            const int i0 = __popc(rel & ((1u << s0) - 1u)), i1 = __popc(rel & ((1u << s1) - 1u));
+            const unsigned long long *r0 = a.sp + (size_t)st.c[i0] * B + 2 * lane;
+            const unsigned long long *r1 = a.sp + (size_t)st.c[i1] * B + 2 * lane;
             unsigned long long x0[2 * W], x1[2 * W];
 #pragma unroll
-            for (int k = 0; k < 2 * W; ++k) {
-                x0[k] = slot_bit<W>(f0, k, lanebit) ? __ldcg(r0 + 32 * k) : 0ull;
-                x1[k] = (two && slot_bit<W>(f1, k, lanebit)) ? __ldcg(r1 + 32 * k) : 0ull;
+            for (int q = 0; q < W; ++q) {
+                const unsigned p0 = pair_bits<W>(st.f[i0][q], lane);
+                const unsigned p1 = two ? pair_bits<W>(st.f[i1][q], lane) : 0u;
+                ulonglong2 v0 = make_ulonglong2(0ull, 0ull), v1 = make_ulonglong2(0ull, 0ull);
+                if (p0) v0 = __ldcg(reinterpret_cast<const ulonglong2 *>(r0 + 64 * q));
+                if (p1) v1 = __ldcg(reinterpret_cast<const ulonglong2 *>(r1 + 64 * q));
+                x0[2 * q] = (p0 & 1u) ? v0.x : 0ull;
+                x0[2 * q + 1] = (p0 & 2u) ? v0.y : 0ull;
+                x1[2 * q] = (p1 & 1u) ? v1.x : 0ull;
+                x1[2 * q + 1] = (p1 & 2u) ? v1.y : 0ull;
             }
 #pragma unroll
             for (int k = 0; k < 2 * W; ++k) {
@@ -253,25 +293,15 @@ __device__ __forceinline__ void gather(const BArgs &a, int beg, int end,
                     e0 = dev::ff_add(e0, dev::ff_mul(sv[k], dev::ff_unpack(x0[k])));
                     e1 = dev::ff_add(e1, dev::ff_mul(sv[k], dev::ff_unpack(x1[k])));
                 }
-                // both sums at once: one exchange leaves neighbour 0's partials in the low
-                // half-warp and neighbour 1's in the high half, then each half reduces alone
-                const bool lo = lane < 16;
-                dev::ff mine = lo ? e0 : e1, other = lo ? e1 : e0;
-                dev::ff recv;
-                recv.hi = __shfl_xor_sync(FULL, other.hi, 16);
-                recv.lo = __shfl_xor_sync(FULL, other.lo, 16);
-                mine = dev::ff_add(mine, recv);
-#pragma unroll
-                for (int o = 8; o > 0; o >>= 1) {
-                    dev::ff y;
-                    y.hi = __shfl_xor_sync(FULL, mine.hi, o);
-                    y.lo = __shfl_xor_sync(FULL, mine.lo, o);
-                    mine = dev::ff_add(mine, y);
+                e0 = dev::group_sum_ff<32>(e0);
+                e1 = dev::group_sum_ff<32>(e1);
+                if (lane == 0) {
+                    a.edge[st.j[i0]] += dev::ff_to_double(e0);
+                    if (two) a.edge[st.j[i1]] += dev::ff_to_double(e1);
                 }
-                if (lane == 0) a.edge[base + s0] += dev::ff_to_double(mine);
-                if (two && lane == 16) a.edge[base + s1] += dev::ff_to_double(mine);
             }
         }
+        __syncwarp();
     }
     if (!PSI) ovf |= carry != 0;
 }
@@ -281,9 +311,9 @@ template <int W> __device__ __forceinline__ Bits<W> nonzero_bits(const unsigned 
     Bits<W> r;
 #pragma unroll
     for (int q = 0; q < W; ++q) {
-        const unsigned lo = __ballot_sync(FULL, acc[2 * q] != 0ull);
-        const unsigned hi = __ballot_sync(FULL, acc[2 * q + 1] != 0ull);
-        r.w[q] = (unsigned long long)lo | ((unsigned long long)hi << 32);
+        const unsigned e0 = __ballot_sync(FULL, acc[2 * q] != 0ull);
+        const unsigned e1 = __ballot_sync(FULL, acc[2 * q + 1] != 0ull);
+        r.w[q] = spread32(e0) | (spread32(e1) << 1);
     }
     return r;
 }
@@ -303,10 +333,10 @@ __device__ __forceinline__ void settle(const BArgs &a, int w, const Bits<W> &vol
 {
     constexpr int B = 64 * W;
     const int lane = threadIdx.x & 31;
-    unsigned long long *row = a.sp + (size_t)w * B + lane;
+    unsigned long long *row = a.sp + (size_t)w * B;
 #pragma unroll
     for (int k = 0; k < 2 * W; ++k)
-        if (has_slot<W>(nb, k, lane)) row[32 * k] = acc[k];
+        if (has_slot<W>(nb, k, lane)) row[slot_off(k, lane)] = acc[k];
     bool full = true;
 #pragma unroll
     for (int q = 0; q < W; ++q) {
@@ -462,26 +492,30 @@ template <class Fn> __device__ __forceinline__ void for_heavy(const BArgs &a, Fn
 template <int W>
 __device__ __forceinline__ void store_part(const BArgs &a, int c, const unsigned long long (&acc)[2 * W])
 {
-    unsigned long long *row = a.part + (size_t)c * (64 * W) + (threadIdx.x & 31);
+    unsigned long long *row = a.part + (size_t)c * (64 * W);
 #pragma unroll
-    for (int k = 0; k < 2 * W; ++k) row[32 * k] = acc[k];
+    for (int k = 0; k < 2 * W; ++k) row[slot_off(k, threadIdx.x & 31)] = acc[k];
 }
 
 __device__ __forceinline__ bool heavy(const BArgs &a, int v) { return deg_of(a.rp, v) > a.chunk; }
 
 template <int W, bool EDGE>
-__global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
+__global__ void __launch_bounds__(kThreads, (W <= 2 ? 4 : 2)) k_batch(BArgs a)
 {
     constexpr int B = 64 * W;
     __shared__ BlockCnt bc;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Nbrs<W> &st = reinterpret_cast<Nbrs<W> *>(smem_raw)[threadIdx.x >> 5];
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nthr = (long long)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
     const size_t slab = (size_t)a.n * W;
+    const int nsrc = a.ksrc ? max(0, min(B, __ldg(a.ksrc) - a.boff)) : a.nsrc;
+    if (nsrc == 0) return;  // uniform over the grid: no barrier is entered
     Bits<W> act;
 #pragma unroll
     for (int q = 0; q < W; ++q) {
-        const int left = a.nsrc - 64 * q;
+        const int left = nsrc - 64 * q;
         act.w[q] = left >= 64 ? ~0ull : (left <= 0 ? 0ull : ((1ull << left) - 1));
     }
     bool ovf = false;
@@ -513,7 +547,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
     }
     if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
     trace_mark(a, ti, 0, PH_INIT);
-    if (tid < a.nsrc) {
+    if (tid < nsrc) {
         const int s = __ldg(a.src + tid);
         const unsigned long long bit = 1ull << (tid & 63);
         atomicOr(a.F + (size_t)s * W + (tid >> 6), bit);
@@ -521,19 +555,19 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
         a.sp[(size_t)s * B + tid] = 1ull;
         a.queue[tid] = s;
         atomicAdd(a.mfv, (unsigned long long)deg_of(a.rp, s));
-        if (a.nsrc == 1) a.dmu[0] = (unsigned long long)deg_of(a.rp, s);
+        if (nsrc == 1) a.dmu[0] = (unsigned long long)deg_of(a.rp, s);
     }
     if (tid == 0) {
-        a.vcnt[0] = a.nsrc;
-        a.qcnt[0] = a.nsrc;
+        a.vcnt[0] = nsrc;
+        a.qcnt[0] = nsrc;
         a.qoff[0] = 0;
     }
     if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
 
     long long mu = a.A - (long long)__ldcg(a.dmu);
     long long mf = (long long)__ldcg(a.mfv);
-    int d = 0, qo = 0, nq = a.nsrc, td = 0, bu = 0;
-    long long qtail = a.nsrc;
+    int d = 0, qo = 0, nq = nsrc, td = 0, bu = 0;
+    long long qtail = nsrc;
     for (;;) {
         if (threadIdx.x == 0) {
             bc.v = 0;
@@ -587,7 +621,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
                     dev::ff facc[2 * W];
 #pragma unroll
                     for (int k = 0; k < 2 * W; ++k) acc[k] = 0;
-                    gather<W, false>(a, __ldg(a.rp + w), __ldg(a.rp + w + 1), Fd, u, acc, facc, ovf);
+                    gather<W, false>(a, __ldg(a.rp + w), __ldg(a.rp + w + 1), Fd, u, acc, facc, ovf, st);
                     const Bits<W> nb = nonzero_bits<W>(acc);
                     if (any_bits<W>(nb)) settle<W>(a, w, vold, nb, act, acc, Fn, &bc);
                 }
@@ -599,7 +633,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
                 dev::ff facc[2 * W];
 #pragma unroll
                 for (int k = 0; k < 2 * W; ++k) acc[k] = 0;
-                gather<W, false>(a, j0, j1, Fd, u, acc, facc, ovf);
+                gather<W, false>(a, j0, j1, Fd, u, acc, facc, ovf, st);
                 store_part<W>(a, c, acc);
             });
             if (a.H > 0 && !dev::grid_barrier(a.ctrl, a.limit_ns)) return;
@@ -612,10 +646,10 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
 #pragma unroll
                 for (int k = 0; k < 2 * W; ++k) acc[k] = 0;
                 for (int c = c0; c < c1; ++c) {
-                    const unsigned long long *row = a.part + (size_t)c * B + lane;
+                    const unsigned long long *row = a.part + (size_t)c * B;
 #pragma unroll
                     for (int k = 0; k < 2 * W; ++k) {
-                        const unsigned long long y = acc[k] + __ldcg(row + 32 * k);
+                        const unsigned long long y = acc[k] + __ldcg(row + slot_off(k, lane));
                         ovf |= y < acc[k];
                         acc[k] = y;
                     }
@@ -668,7 +702,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
                 dev::ff facc[2 * W];
 #pragma unroll
                 for (int k = 0; k < 2 * W; ++k) acc[k] = 0;
-                gather<W, false>(a, __ldg(a.rp + w), __ldg(a.rp + w + 1), Fd, t, acc, facc, ovf);
+                gather<W, false>(a, __ldg(a.rp + w), __ldg(a.rp + w + 1), Fd, t, acc, facc, ovf, st);
                 settle<W>(a, w, vold, t, act, acc, nullptr, &bc);
             });
             for_chunks(a, a.wq + (size_t)d * 8 + WQ_PULL_C, [&](int c, int h, int j0, int j1) {
@@ -678,7 +712,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
                 dev::ff facc[2 * W];
 #pragma unroll
                 for (int k = 0; k < 2 * W; ++k) acc[k] = 0;
-                gather<W, false>(a, j0, j1, Fd, t, acc, facc, ovf);
+                gather<W, false>(a, j0, j1, Fd, t, acc, facc, ovf, st);
                 store_part<W>(a, c, acc);
             });
             if (a.H > 0 && !dev::grid_barrier(a.ctrl, a.limit_ns)) return;
@@ -692,10 +726,10 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
 #pragma unroll
                 for (int k = 0; k < 2 * W; ++k) acc[k] = 0;
                 for (int c = c0; c < c1; ++c) {
-                    const unsigned long long *row = a.part + (size_t)c * B + lane;
+                    const unsigned long long *row = a.part + (size_t)c * B;
 #pragma unroll
                     for (int k = 0; k < 2 * W; ++k) {
-                        const unsigned long long y = acc[k] + __ldcg(row + 32 * k);
+                        const unsigned long long y = acc[k] + __ldcg(row + slot_off(k, lane));
                         ovf |= y < acc[k];
                         acc[k] = y;
                     }
@@ -742,7 +776,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
         // order.  Every vertex strictly between the source and the target is counted.
         // The slabs and sigma rows are complete: the last level ended with a grid barrier.
         const long long wid = tid >> 5, nw = nthr >> 5;
-        for (long long b = wid; b < a.nsrc; b += nw) {
+        for (long long b = wid; b < nsrc; b += nw) {
             const int v = __ldg(a.rk_t + b);
             const int q = (int)(b >> 6);
             const unsigned long long bit = 1ull << (b & 63);
@@ -826,13 +860,13 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
         // source slots goes to the FP64 score once per vertex and level
         auto finish = [&](int v, const Bits<W> &mv, const dev::ff (&facc)[2 * W]) {
             dev::ff part = dev::ff_zero();
-            unsigned long long *row = a.sp + (size_t)v * B + lane;
+            unsigned long long *row = a.sp + (size_t)v * B;
 #pragma unroll
             for (int k = 0; k < 2 * W; ++k) {
                 if (has_slot<W>(mv, k, lane)) {
-                    const dev::ff sv = dev::ff_from_u64(__ldcg(row + 32 * k));
+                    const dev::ff sv = dev::ff_from_u64(__ldcg(row + slot_off(k, lane)));
                     const dev::ff delta = dev::ff_mul(sv, facc[k]);
-                    row[32 * k] = dev::ff_pack(dev::ff_add(dev::ff_rcp(sv), facc[k]));
+                    row[slot_off(k, lane)] = dev::ff_pack(dev::ff_add(dev::ff_rcp(sv), facc[k]));
                     part = dev::ff_add(part, delta);
                 }
             }
@@ -842,10 +876,10 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
         // sigma_b(v) of the lane's slots in mv (edge betweenness only), read before psi
         // replaces it
         auto sigma_row = [&](int v, const Bits<W> &mv, dev::ff (&sv)[2 * W]) {
-            const unsigned long long *row = a.sp + (size_t)v * B + lane;
+            const unsigned long long *row = a.sp + (size_t)v * B;
 #pragma unroll
             for (int k = 0; k < 2 * W; ++k)
-                sv[k] = has_slot<W>(mv, k, lane) ? dev::ff_from_u64(__ldcg(row + 32 * k)) : dev::ff_zero();
+                sv[k] = has_slot<W>(mv, k, lane) ? dev::ff_from_u64(__ldcg(row + slot_off(k, lane))) : dev::ff_zero();
         };
         for_level<W>(a, ql, nl, Fl, a.wq + (size_t)l * 8 + WQ_BACK, [&](int v) {
             if (heavy(a, v)) return;
@@ -856,7 +890,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
             for (int k = 0; k < 2 * W; ++k) facc[k] = dev::ff_zero();
             if constexpr (EDGE) sigma_row(v, mv, sv);
             bool dummy = false;
-            gather<W, true, EDGE>(a, __ldg(a.rp + v), __ldg(a.rp + v + 1), Fs, mv, acc, facc, dummy, sv);
+            gather<W, true, EDGE>(a, __ldg(a.rp + v), __ldg(a.rp + v + 1), Fs, mv, acc, facc, dummy, st, sv);
             finish(v, mv, facc);
         });
         for_chunks(a, a.wq + (size_t)l * 8 + WQ_BACK_C, [&](int c, int h, int j0, int j1) {
@@ -868,7 +902,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
             for (int k = 0; k < 2 * W; ++k) facc[k] = dev::ff_zero();
             if constexpr (EDGE) sigma_row(h, mv, sv);
             bool dummy = false;
-            gather<W, true, EDGE>(a, j0, j1, Fs, mv, acc, facc, dummy, sv);
+            gather<W, true, EDGE>(a, j0, j1, Fs, mv, acc, facc, dummy, st, sv);
 #pragma unroll
             for (int k = 0; k < 2 * W; ++k) acc[k] = dev::ff_pack(facc[k]);
             store_part<W>(a, c, acc);
@@ -882,9 +916,9 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
 #pragma unroll
             for (int k = 0; k < 2 * W; ++k) facc[k] = dev::ff_zero();
             for (int c = c0; c < c1; ++c) {
-                const unsigned long long *row = a.part + (size_t)c * B + lane;
+                const unsigned long long *row = a.part + (size_t)c * B;
 #pragma unroll
-                for (int k = 0; k < 2 * W; ++k) facc[k] = dev::ff_add(facc[k], dev::ff_unpack(__ldcg(row + 32 * k)));
+                for (int k = 0; k < 2 * W; ++k) facc[k] = dev::ff_add(facc[k], dev::ff_unpack(__ldcg(row + slot_off(k, lane))));
             }
             finish(h, mv, facc);
         });
@@ -894,12 +928,18 @@ __global__ void __launch_bounds__(kThreads) k_batch(BArgs a)
 }
 
 // ------------------------------------------------------------------ host side
+// Dynamic shared memory of one CTA: a neighbour list per warp.
+template <int W> constexpr size_t smem_bytes() { return (size_t)(kThreads / 32) * sizeof(Nbrs<W>); }
+
+// Co-resident CTAs per SM of k_batch<W, EDGE> with its shared memory (the shared-memory
+// attribute is set on the first call, outside any stream capture).
 template <int W, bool EDGE = false> int blocks_per_sm()
 {
     static int b = -1;
     if (b < 0) {
+        NK_CUDA(cudaFuncSetAttribute(k_batch<W, EDGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<W>()));
         int v = 0;
-        NK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_batch<W, EDGE>, kThreads, 0));
+        NK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_batch<W, EDGE>, kThreads, smem_bytes<W>()));
         b = v;
     }
     return b;
@@ -972,6 +1012,27 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
                    const RunCfg &cfg, RunStats *st, cudaStream_t s)
 {
     constexpr int B = 64 * W;
+    // sources without arcs add nothing: the batches take the others (the error-bounded
+    // estimate keeps its slots, which are tied to their targets)
+    Tmp csrc, ccnt;
+    if (!cfg.rk_t) {
+        NK_TRY(csrc.alloc(sizeof(int32_t) * (size_t)k, s));
+        NK_TRY(ccnt.alloc(sizeof(int32_t), s));
+        NK_TRY(compact_sources(g, d_src, k, csrc.as<int32_t>(), ccnt.as<int32_t>(), s));
+        int32_t kk = 0;
+        NK_CUDA(cudaMemcpyAsync(&kk, ccnt.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        NK_CUDA(cudaStreamSynchronize(s));
+        if (kk < 0 || kk > k) return set_error(NK_ERR_CUDA, "source compaction returned %d of %d", kk, k);
+        d_src = csrc.as<int32_t>();
+        k = kk;
+        if (k == 0) {
+            if (st) {
+                st->mode = NK_MODE_BATCHED;
+                st->batch = B;
+            }
+            return NK_OK;
+        }
+    }
     HeavyView hw;
     NK_TRY(heavy_view(g, cfg.chunk, s, &hw));
     DevBuf *ws = scratch(cfg, g);
@@ -1002,7 +1063,7 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
         const Layout L = layout(g, B, lcap, hw.chunk);
         NK_TRY(ws[WS_BATCH].ensure(L.total));
         char *base = ws[WS_BATCH].as<char>();
-        BArgs a;
+        BArgs a{};
         a.n = g->n;
         a.A = g->A;
         a.rp = g->rp.as<int32_t>();
@@ -1046,6 +1107,8 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
             NK_CUDA(cudaEventCreate(&e1));
             NK_CUDA(cudaEventRecord(e0, s));
         }
+        a.ksrc = nullptr;
+        a.boff = 0;
         for (int bi : todo) {
             a.src = d_src + (size_t)bi * B;
             a.nsrc = std::min(B, k - bi * B);
@@ -1054,13 +1117,13 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
             a.rk_key = cfg.rk_key ? cfg.rk_key + (size_t)bi * B : nullptr;
             a.trace = (trace_on && bi == todo.front()) ? trace_buf.as<unsigned long long>() : nullptr;
             void *args[] = {&a};
-            NK_CUDA(cudaLaunchCooperativeKernel(kfn, dim3(grid), dim3(kThreads), args, 0, s));
+            NK_CUDA(cudaLaunchCooperativeKernel(kfn, dim3(grid), dim3(kThreads), args, smem_bytes<W>(), s));
             ::nk::count_launch();
         }
         if (cfg.time_kernels) NK_CUDA(cudaEventRecord(e1, s));
         std::vector<Ctrl> h(nb);
         NK_CUDA(cudaMemcpyAsync(h.data(), ctrls, sizeof(Ctrl) * nb, cudaMemcpyDeviceToHost, s));
-        NK_CUDA(cudaStreamSynchronize(s));
+        NK_TRY(host_wait(s, (int64_t)todo.size(), a.limit_ns));
         if (st) {
             st->mode = NK_MODE_BATCHED;
             st->batch = B;
@@ -1142,20 +1205,23 @@ int enqueue_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scor
     if (lcap < 4) return set_error(NK_ERR_NOMEM, "not enough device memory for a batch of %d sources", B);
     const int nb = (k + B - 1) / B;
     const Layout L = layout(g, B, lcap, hw.chunk);
+    // status words of the nb batches, then the compacted sources and their count
+    const size_t ctrl_bytes = align_up(sizeof(Ctrl) * nb);
+    const size_t bctrl_bytes = ctrl_bytes + align_up(sizeof(int32_t) * (size_t)k) + 256;
     if (prepare_only) {
         NK_TRY(ws[WS_BATCH].ensure(L.total));
-        NK_TRY(ws[WS_BCTRL].ensure(sizeof(Ctrl) * nb));
+        NK_TRY(ws[WS_BCTRL].ensure(bctrl_bytes));
         if (blocks_per_sm<W>() < 1) return set_error(NK_ERR_CUDA, "batched kernel cannot be resident");
         return NK_OK;
     }
-    if (ws[WS_BATCH].bytes < L.total || ws[WS_BCTRL].bytes < sizeof(Ctrl) * nb)
+    if (ws[WS_BATCH].bytes < L.total || ws[WS_BCTRL].bytes < bctrl_bytes)
         return set_error(NK_ERR_ARG, "batched workspace not prepared");
     const int bps = blocks_per_sm<W>();
     if (bps < 1) return set_error(NK_ERR_CUDA, "batched kernel cannot be resident");
     int grid = std::max(1, bps * num_sms() / std::max(1, cfg.grid_div));
     if (cfg.grid_ctas > 0) grid = std::min(grid, cfg.grid_ctas);
     char *base = ws[WS_BATCH].as<char>();
-    BArgs a;
+    BArgs a{};
     a.n = g->n;
     a.A = g->A;
     a.rp = g->rp.as<int32_t>();
@@ -1195,20 +1261,26 @@ int enqueue_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scor
     a.alpha = cfg.alpha > 0 ? cfg.alpha : 1.0;
     a.dir = cfg.direction;
     Ctrl *ctrls = ws[WS_BCTRL].as<Ctrl>();
+    int32_t *csrc = reinterpret_cast<int32_t *>(ws[WS_BCTRL].as<char>() + ctrl_bytes);
+    int32_t *ccnt = reinterpret_cast<int32_t *>(ws[WS_BCTRL].as<char>() + ctrl_bytes + align_up(sizeof(int32_t) * (size_t)k));
     NK_CUDA(cudaMemsetAsync(ctrls, 0, sizeof(Ctrl) * nb, s));
+    // sources without arcs add nothing: compacted on the device, each batch reads the count
+    NK_TRY(compact_sources(g, d_src, k, csrc, ccnt, s));
+    a.ksrc = ccnt;
     cudaLaunchAttribute attr;
     attr.id = cudaLaunchAttributeCooperative;
     attr.val.cooperative = 1;
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(grid);
     lc.blockDim = dim3(kThreads);
-    lc.dynamicSmemBytes = 0;
+    lc.dynamicSmemBytes = smem_bytes<W>();
     lc.stream = s;
     lc.attrs = &attr;
     lc.numAttrs = 1;
     for (int bi = 0; bi < nb; ++bi) {
-        a.src = d_src + (size_t)bi * B;
+        a.src = csrc + (size_t)bi * B;
         a.nsrc = std::min(B, k - bi * B);
+        a.boff = bi * B;
         a.ctrl = ctrls + bi;
         void *args[] = {&a};
         NK_CUDA(cudaLaunchKernelExC(&lc, (const void *)k_batch<W, false>, args));

@@ -1,8 +1,10 @@
 // Core runtime of libnk: error state, stream selection, device buffers, the prefix-sum
 // primitive, and the bounded-wait self test.
+#include <chrono>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 
 #include "nk_device.cuh"
 #include "nk_internal.h"
@@ -96,6 +98,35 @@ int Tmp::alloc(size_t b, cudaStream_t s)
 Tmp::~Tmp()
 {
     if (p) cudaFreeAsync(p, st);
+}
+
+// ---------------------------------------------------------------- bounded host wait
+int host_wait(cudaStream_t s, int64_t launches, uint64_t limit_ns)
+{
+    cudaEvent_t ev = nullptr;
+    NK_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ev, s);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(ev);
+        return cuda_fail(e, "cudaEventRecord", __FILE__, __LINE__);
+    }
+    const double budget_s = (double)(launches + 1) * 64.0 * (double)limit_ns * 1e-9;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        e = cudaEventQuery(ev);
+        if (e != cudaErrorNotReady) break;
+        const double waited = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (waited > budget_s) {
+            cudaEventDestroy(ev);
+            return set_error(NK_ERR_TIMEOUT, "the host gave up waiting for %lld launches after %.0f s",
+                             (long long)launches, waited);
+        }
+        if (waited < 2e-3) std::this_thread::yield();
+        else std::this_thread::sleep_for(std::chrono::microseconds(100));
+    }
+    cudaEventDestroy(ev);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel execution", __FILE__, __LINE__);
+    return NK_OK;
 }
 
 // ---------------------------------------------------------------- exclusive scan
@@ -200,6 +231,61 @@ int scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t count, int64_t *
             NK_CUDA(cudaMemsetAsync(total, 0, sizeof(int64_t), st));
         }
     }
+    return NK_OK;
+}
+
+// ---------------------------------------------------------------- sources with arcs
+namespace {
+constexpr int kCompactThreads = 1024;
+
+// Stable compaction by one CTA: out[0..count) = the sources of src[0..k) with at least one
+// arc, in their order; *count receives their number.  Tiles of 1024 sources: a flag per
+// thread, warp ballots, a scan of the 32 warp counts, and a running offset.
+__global__ void __launch_bounds__(kCompactThreads)
+k_compact_sources(const int32_t *rp, const int32_t *src, int32_t k, int32_t *out, int32_t *count)
+{
+    __shared__ int warp_cnt[32];
+    __shared__ int tile_base;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) tile_base = 0;
+    __syncthreads();
+    for (int64_t t0 = 0; t0 < k; t0 += kCompactThreads) {
+        const int64_t i = t0 + threadIdx.x;
+        int v = 0;
+        bool keep = false;
+        if (i < k) {
+            v = src[i];
+            keep = rp[v + 1] > rp[v];
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) warp_cnt[wid] = __popc(m);
+        __syncthreads();
+        if (wid == 0) {
+            int x = warp_cnt[lane], incl = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            warp_cnt[lane] = incl - x;  // exclusive over warps
+        }
+        __syncthreads();
+        const int base = tile_base;
+        if (keep) out[base + warp_cnt[wid] + __popc(m & ((1u << lane) - 1u))] = v;
+        __syncthreads();
+        if (threadIdx.x == kCompactThreads - 1) tile_base = base + warp_cnt[wid] + __popc(m);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = tile_base;
+}
+}  // namespace
+
+int compact_sources(const nk_graph *g, const int32_t *d_src, int32_t k, int32_t *d_out, int32_t *d_count,
+                    cudaStream_t s)
+{
+    k_compact_sources<<<1, kCompactThreads, 0, s>>>(g->rp.as<int32_t>(), d_src, k, d_out, d_count);
+    ::nk::count_launch();
+    NK_CUDA(cudaGetLastError());
     return NK_OK;
 }
 

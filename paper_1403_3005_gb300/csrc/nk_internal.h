@@ -45,6 +45,12 @@ cudaStream_t stream();
 uint64_t wait_limit_ns();
 int num_sms();
 
+// Waits for the work queued on s.  Every device-side wait and work loop of the sweeps is
+// bounded by limit_ns, so their launches end by themselves; the host still gives up after
+// (launches + 1) x 64 x limit_ns of wall time and returns NK_ERR_TIMEOUT, so that a call
+// never blocks its caller without end.
+int host_wait(cudaStream_t s, int64_t launches, uint64_t limit_ns);
+
 // ---------------------------------------------------------------- device buffers
 // A growable device allocation; contents are not preserved on growth.  With a stream
 // set (`st`), allocation and release are stream-ordered (cudaMallocAsync /
@@ -274,6 +280,13 @@ inline DevBuf *scratch(const RunCfg &c, nk_graph *g) { return c.ws ? c.ws : g->w
 
 // Device bytes of a batched run with B sources per batch and lcap level slabs.
 size_t batched_bytes_lcap(const nk_graph *g, int B, int lcap);
+
+// Stable compaction of the sources that have at least one arc: d_out[0..*d_count) (device)
+// receives them in their order.  A source without arcs reaches no vertex, so its
+// dependencies, its arc shares and its distance sums are all zero: the sweeps skip it.
+// One CTA, no allocation (usable inside a stream capture); the ids must be in range.
+int compact_sources(const nk_graph *g, const int32_t *d_src, int32_t k, int32_t *d_out, int32_t *d_count,
+                    cudaStream_t s);
 
 // Scale a device vector in place.
 int scale_vector(double *d, int32_t n, double scale, cudaStream_t s);

@@ -545,6 +545,21 @@ int run(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores, const Ru
         NK_CUDA(cudaEventRecord(e0, s));
     }
     if (cfg.far || cfg.rk_t) a.forward_only = 1;
+    // sources without arcs add nothing to scores, arc shares or distance sums: only the
+    // others are swept (not for a single-source sweep, whose outputs the caller reads, nor
+    // for the error-bounded estimate, whose sources are tied to their targets)
+    Tmp csrc, ccnt;
+    if (!d_dist_out && !cfg.rk_t && k > 0) {
+        NK_TRY(csrc.alloc(sizeof(int32_t) * (size_t)k, s));
+        NK_TRY(ccnt.alloc(sizeof(int32_t), s));
+        NK_TRY(compact_sources(g, d_src, k, csrc.as<int32_t>(), ccnt.as<int32_t>(), s));
+        int32_t kk = 0;
+        NK_CUDA(cudaMemcpyAsync(&kk, ccnt.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        NK_CUDA(cudaStreamSynchronize(s));
+        if (kk < 0 || kk > k) return set_error(NK_ERR_CUDA, "source compaction returned %d of %d", kk, k);
+        d_src = csrc.as<int32_t>();
+        k = kk;
+    }
     for (int32_t i = 0; i < k; ++i) {
         a.src = d_src + i;
         void *args[] = {&a};
@@ -564,7 +579,7 @@ int run(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores, const Ru
     if (cfg.time_kernels) NK_CUDA(cudaEventRecord(e1, s));
     Ctrl h;
     NK_CUDA(cudaMemcpyAsync(&h, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
-    NK_CUDA(cudaStreamSynchronize(s));
+    NK_TRY(host_wait(s, k, a.limit_ns));
     if (st) {
         st->mode = NK_MODE_PER_SOURCE;
         st->batch = 1;

@@ -463,7 +463,7 @@ int run_weighted(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores,
     if (sigma_out) NK_CUDA(cudaMemcpyAsync(sigma_out, a.sp, sizeof(uint64_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
     std::vector<Ctrl> h(G);
     NK_CUDA(cudaMemcpyAsync(h.data(), a.ctrl, sizeof(Ctrl) * G, cudaMemcpyDeviceToHost, s));
-    NK_CUDA(cudaStreamSynchronize(s));
+    NK_TRY(host_wait(s, k, a.limit_ns));  // one launch runs the k searches
     int err = 0, ovf = 0, depth = 0;
     for (const Ctrl &c : h) {
         err = err ? err : c.err;

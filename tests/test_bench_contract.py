@@ -11,10 +11,25 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
 
+def test_default_workload_is_the_headline_config():
+    # with no flags, bench.py measures R-MAT scale 24 with k = 8192 sampled sources
+    import bench
+    saved = sys.argv
+    try:
+        sys.argv = ["bench.py"]
+        args = bench.parse()
+    finally:
+        sys.argv = saved
+    assert args.config == "rmat24" and args.gpus == 1 and args.warmup >= 3
+    cfg = bench.CONFIGS[args.config]
+    assert (cfg["kind"], cfg["size"], cfg["k"]) == ("rmat", 24, 8192)
+
+
 def test_reference_arm_json_line():
+    # the contract's keys do not depend on the workload: the small config keeps this quick
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                          "--steps", "1", "--warmup", "0"], capture_output=True, text=True, timeout=600,
-                         cwd=ROOT)
+                          "--config", "rmat18", "--steps", "1", "--warmup", "0"], capture_output=True,
+                         text=True, timeout=600, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.strip().startswith("{")]
     assert len(lines) == 1
