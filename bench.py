@@ -247,17 +247,34 @@ def serving_load(nk, torch, n_req, seed=3):
     srv = nk.Server()
     t0 = time.perf_counter()
     next_t = t0
-    ids = []
+    ids, outs = [], []
     for (g, s, k), gap in zip(reqs, gaps):
         next_t += gap
         while time.perf_counter() < next_t:
             time.sleep(min(0.0005, max(0.0, next_t - time.perf_counter())))
-        ids.append(srv.submit(g, s, k)[0])
+        rid, res = srv.submit(g, s, k)
+        ids.append(rid)
+        outs.append(res)
     for i in ids:
         assert srv.wait(i, 600.0) == 0
     wall = time.perf_counter() - t0
     st = srv.stats()
     srv.close()
+    # a seeded 5 % of the requests again, each alone on an idle server: the in-mix result
+    # must match (packing changes only the order of floating-point sums)
+    pick = np.sort(np.random.default_rng(seed + 1).choice(len(reqs), max(1, len(reqs) // 20), replace=False))
+    worst, ok = 0.0, True
+    for i in pick:
+        g, s, k = reqs[i]
+        alone = nk.Server()
+        rid, res = alone.submit(g, s, k)
+        assert alone.wait(rid, 600.0) == 0
+        alone.close()
+        mix = outs[i]
+        nz = res != 0
+        if np.any(nz):
+            worst = max(worst, float(np.max(np.abs(mix[nz] - res[nz]) / np.abs(res[nz]))))
+        ok &= bool(np.allclose(mix, res, rtol=1e-9, atol=1e-12))
     for g, _, _ in reqs:
         g.free()
     return {"requests": len(reqs), "capacity_req_per_s": cap, "arrival_rate_req_per_s": lam,
@@ -269,7 +286,8 @@ def serving_load(nk, torch, n_req, seed=3):
             "peak_inflight": st["peak_inflight"], "peak_bytes": st["peak_bytes"],
             "closed_loop_gteps": cst["edges_x_sources"] / closed_s / 1e9,
             "closed_loop_p50_ms": cst["p50_ms"], "closed_loop_p99_ms": cst["p99_ms"],
-            "closed_loop_launches": cst["jobs"], "closed_loop_packed_requests": cst["packed_requests"]}
+            "closed_loop_launches": cst["jobs"], "closed_loop_packed_requests": cst["packed_requests"],
+            "alone_checked": int(len(pick)), "alone_max_rel_diff": worst, "alone_within_1e-9": ok}
 
 
 def host_info():

@@ -253,52 +253,75 @@ __device__ __forceinline__ void gather(const BArgs &a, int beg, int end,
             for (int q = 0; q < W; ++q) st.f[pos][q] = f.w[q];
         }
         __syncwarp();
+        // NB relevant neighbours per round (two for the edge variant): every load of the
+        // round is issued before any addition, so their latencies overlap
+        constexpr int NB = 2;
         unsigned left = rel;
         while (left) {
-            const int s0 = __ffs(left) - 1;
-            left &= left - 1;
-            const bool two = left != 0;
-            const int s1 = two ? __ffs(left) - 1 : s0;
-            if (two) left &= left - 1;
-            const int i0 = __popc(rel & ((1u << s0) - 1u)), i1 = __popc(rel & ((1u << s1) - 1u));
-            const unsigned long long *r0 = a.sp + (size_t)st.c[i0] * B + 2 * lane;
-            const unsigned long long *r1 = a.sp + (size_t)st.c[i1] * B + 2 * lane;
-            unsigned long long x0[2 * W], x1[2 * W];
+            int idx[NB];
+            bool on[NB];
 #pragma unroll
-            for (int q = 0; q < W; ++q) {
-                const unsigned p0 = pair_bits<W>(st.f[i0][q], lane);
-                const unsigned p1 = two ? pair_bits<W>(st.f[i1][q], lane) : 0u;
-                ulonglong2 v0 = make_ulonglong2(0ull, 0ull), v1 = make_ulonglong2(0ull, 0ull);
-                if (p0) v0 = __ldcg(reinterpret_cast<const ulonglong2 *>(r0 + 64 * q));
-                if (p1) v1 = __ldcg(reinterpret_cast<const ulonglong2 *>(r1 + 64 * q));
-                x0[2 * q] = (p0 & 1u) ? v0.x : 0ull;
-                x0[2 * q + 1] = (p0 & 2u) ? v0.y : 0ull;
-                x1[2 * q] = (p1 & 1u) ? v1.x : 0ull;
-                x1[2 * q + 1] = (p1 & 2u) ? v1.y : 0ull;
+            for (int r = 0; r < NB; ++r) {
+                on[r] = left != 0;
+                const int sr = on[r] ? __ffs(left) - 1 : 0;
+                if (on[r]) left &= left - 1;
+                idx[r] = on[r] ? __popc(rel & ((1u << sr) - 1u)) : 0;
             }
+            ulonglong2 v[NB][W];
+            unsigned pb[NB][W];
+#pragma unroll
+            for (int r = 0; r < NB; ++r) {
+                const unsigned long long *row = a.sp + (size_t)st.c[idx[r]] * B + 2 * lane;
+#pragma unroll
+                for (int q = 0; q < W; ++q) {
+                    pb[r][q] = on[r] ? pair_bits<W>(st.f[idx[r]][q], lane) : 0u;
+                    v[r][q] = make_ulonglong2(0ull, 0ull);
+                    if (pb[r][q]) v[r][q] = __ldcg(reinterpret_cast<const ulonglong2 *>(row + 64 * q));
+                }
+            }
+            unsigned long long x[NB][2 * W];
+#pragma unroll
+            for (int r = 0; r < NB; ++r)
+#pragma unroll
+                for (int q = 0; q < W; ++q) {
+                    x[r][2 * q] = (pb[r][q] & 1u) ? v[r][q].x : 0ull;
+                    x[r][2 * q + 1] = (pb[r][q] & 2u) ? v[r][q].y : 0ull;
+                }
 #pragma unroll
             for (int k = 0; k < 2 * W; ++k) {
-                if constexpr (PSI) {
-                    facc[k] = dev::ff_add(facc[k], dev::ff_unpack(x0[k]));
-                    facc[k] = dev::ff_add(facc[k], dev::ff_unpack(x1[k]));
-                } else {
-                    add_carry(acc[k], carry, x0[k]);
-                    add_carry(acc[k], carry, x1[k]);
+#pragma unroll
+                for (int r = 0; r < NB; ++r) {
+                    if constexpr (PSI) {
+                        facc[k] = dev::ff_add(facc[k], dev::ff_unpack(x[r][k]));
+                    } else {
+                        add_carry(acc[k], carry, x[r][k]);
+                    }
                 }
             }
             if constexpr (EDGE) {
                 dev::ff e0 = dev::ff_zero(), e1 = dev::ff_zero();
 #pragma unroll
                 for (int k = 0; k < 2 * W; ++k) {
-                    e0 = dev::ff_add(e0, dev::ff_mul(sv[k], dev::ff_unpack(x0[k])));
-                    e1 = dev::ff_add(e1, dev::ff_mul(sv[k], dev::ff_unpack(x1[k])));
+                    e0 = dev::ff_add(e0, dev::ff_mul(sv[k], dev::ff_unpack(x[0][k])));
+                    e1 = dev::ff_add(e1, dev::ff_mul(sv[k], dev::ff_unpack(x[NB - 1][k])));
                 }
-                e0 = dev::group_sum_ff<32>(e0);
-                e1 = dev::group_sum_ff<32>(e1);
-                if (lane == 0) {
-                    a.edge[st.j[i0]] += dev::ff_to_double(e0);
-                    if (two) a.edge[st.j[i1]] += dev::ff_to_double(e1);
+                // both sums at once: one exchange leaves neighbour 0's partials in the low
+                // half-warp and neighbour 1's in the high half, then each half reduces alone
+                const bool lo = lane < 16;
+                dev::ff mine = lo ? e0 : e1, other = lo ? e1 : e0;
+                dev::ff recv;
+                recv.hi = __shfl_xor_sync(FULL, other.hi, 16);
+                recv.lo = __shfl_xor_sync(FULL, other.lo, 16);
+                mine = dev::ff_add(mine, recv);
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) {
+                    dev::ff y;
+                    y.hi = __shfl_xor_sync(FULL, mine.hi, o);
+                    y.lo = __shfl_xor_sync(FULL, mine.lo, o);
+                    mine = dev::ff_add(mine, y);
                 }
+                if (lane == 0) a.edge[st.j[idx[0]]] += dev::ff_to_double(mine);
+                if (on[NB - 1] && lane == 16) a.edge[st.j[idx[NB - 1]]] += dev::ff_to_double(mine);
             }
         }
         __syncwarp();

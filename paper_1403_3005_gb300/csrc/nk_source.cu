@@ -3,27 +3,35 @@
 // measured against, and the fallback for very deep BFS trees.
 //
 // One cooperative (co-resident) launch per source runs every level of that source:
-//   init      dist = -1, sigma = 0; dist[s] = 0, sigma[s] = 1
-//   forward   level-synchronous BFS (Section 3.4: BFS for unweighted graphs); per level
-//             either
-//             - top-down: groups of TPV lanes expand the frontier vertices; atomicCAS on
-//               dist claims a vertex for level d+1 and appends it to the queue
-//               (warp-aggregated), and every arc (v,w) with dist[w] = d+1 adds sigma[v]
-//               to sigma[w] (atomicAdd; a carry out of 64 bits is flagged), or
-//             - bottom-up: every unvisited w sums sigma[v] over ALL neighbours v at
-//               level d (no early exit: sigma needs every parent) and joins level d+1 if
-//               the sum is non-zero; levels found this way are not queued and are later
-//               iterated by scanning dist;
+//   init      dist = -1, sigma = 0; dist[s] = 0, sigma[s] = 1; the bitmaps are cleared
+//   forward   level-synchronous BFS (Section 3.4: BFS for unweighted graphs).  Three
+//             bitmaps of n bits, small enough to stay in L2, carry the frontier: `vis`
+//             (levels found so far) and the level bitmaps `lvl[d & 1]` of levels d and
+//             d+1.  Every level's vertices are also appended to one queue (warp-aggregated:
+//             one atomic per warp and ballot ranks), so every level can be iterated from
+//             its queue segment.  Per level either
+//             - top-down: warps take up to 32 frontier vertices at a time from the queue,
+//               stage their ids, sigma and arc offsets in shared memory and run lanes over
+//               the concatenated arc list, so that low-degree vertices do not leave lanes
+//               idle; for an arc (v, w) with w not in `vis`, an atomicOr on the level-(d+1)
+//               bitmap claims w (the claiming lane queues it) and sigma[v] is added to
+//               sigma[w] (atomicAdd; a carry out of 64 bits is flagged), or
+//             - bottom-up: every unvisited w (a bit test on `vis`, 32 vertices per word)
+//               sums sigma[v] over ALL neighbours v in the level-d bitmap (no early exit:
+//               sigma needs every parent) and joins level d+1 if the sum is non-zero;
 //             bottom-up is chosen when alpha * (arcs of the frontier) > (arcs of the
-//             unvisited vertices).
-//   backward  deepest level first, every v at level d pulls from its successors:
+//             unvisited vertices).  Rows longer than kHeavyChunk arcs are split into
+//             chunks, read with 16-byte column loads by a warp each.
+//   backward  deepest level first; the level bitmap is rebuilt for level d+1 from its
+//             queue segment, and every v at level d (from its queue segment) pulls from its
+//             successors (neighbours in that bitmap):
 //               acc = sum_{w in N(v), dist w = d+1} psi[w],  psi = (1 + delta) / sigma,
 //               delta_s(v) = sigma[v] * acc,  scores[v] += delta_s(v),
 //             which is Brandes' recurrence delta(v) = sum sigma_v/sigma_w (1 + delta_w)
 //             with the common factor sigma_v taken out; psi_v = 1/sigma_v + acc.  The
-//             sums run in double-single arithmetic (FP32 pipe), scores in FP64.  psi overwrites sigma in place
-//             once a vertex's level is done (sigma of level d is still intact while
-//             level d reads psi of level d+1).
+//             sums run in double-single arithmetic (FP32 pipe), scores in FP64.  psi
+//             overwrites sigma in place once a vertex's level is done (sigma of level d is
+//             still intact while level d reads psi of level d+1).
 // The levels are separated by a bounded grid barrier; per-level counters live in
 // arrays indexed by level, so every CTA reads the same values after a barrier.
 #include <cooperative_groups.h>
@@ -41,6 +49,7 @@ namespace nk {
 namespace {
 
 constexpr int kThreads = 512;
+constexpr unsigned FULL = 0xffffffffu;
 
 struct SrcArgs {
     int32_t n;
@@ -49,10 +58,10 @@ struct SrcArgs {
     const int32_t *src;  // the source is *src
     int32_t *dist;
     unsigned long long *sp;  // sigma during the forward sweep, then psi (double bits)
-    int32_t *queue;
+    int32_t *queue;      // [n] the vertices of every level, level by level
     int32_t *cnt;        // cnt[d]: vertices at level d
     long long *mfa;      // mfa[d]: sum of the degrees of level d
-    int32_t *qoff;       // qoff[d]: start of level d in queue, -1 if level d is not queued
+    int32_t *qoff;       // qoff[d]: start of level d in queue
     double *scores;      // += delta_s (not touched when forward_only)
     Ctrl *ctrl;
     uint64_t limit_ns;
@@ -64,6 +73,9 @@ struct SrcArgs {
     const int32_t *hv, *hfirst, *chunk_h;
     int32_t H, C;
     unsigned long long *part;
+    // bitmaps of nw = ceil(n / 32) words each: vis, then the two level bitmaps
+    unsigned *bits;
+    int32_t nw;
 };
 
 template <int TPV> struct Lanes {
@@ -94,132 +106,188 @@ __device__ __forceinline__ void chunk_of(const SrcArgs &a, long long c, int &h, 
     j1 = min(j0 + kHeavyChunk, __ldg(a.rp + h + 1));
 }
 
-// One arc (v, w) of a top-down step from level d: claim w for level d+1 (queued once,
-// warp-aggregated), and add sigma[v] if w is at level d+1.
+// bitmaps: vis = bits[0, nw), level bitmap p = bits[(1 + p) nw, (2 + p) nw)
+__device__ __forceinline__ unsigned *vis_bits(const SrcArgs &a) { return a.bits; }
+__device__ __forceinline__ unsigned *lvl_bits(const SrcArgs &a, int p) { return a.bits + (size_t)(1 + (p & 1)) * a.nw; }
+// bit v of a bitmap written earlier in the launch (read from L2: L1 is not coherent)
+__device__ __forceinline__ bool test_bit(const unsigned *b, int v) { return (__ldcg(b + (v >> 5)) >> (v & 31)) & 1u; }
+
+// Appends w to level d+1's queue segment (starting at qnext): the lanes that append
+// together share one atomicAdd and take ranks within the group.
+__device__ __forceinline__ void queue_append(const SrcArgs &a, int d, int qnext, int w)
+{
+    cg::coalesced_group g = cg::coalesced_threads();
+    int pos = 0;
+    if (g.thread_rank() == 0) pos = atomicAdd(a.cnt + d + 1, (int)g.size());
+    pos = g.shfl(pos, 0) + (int)g.thread_rank();
+    if (qnext + pos < a.n) a.queue[qnext + pos] = w;
+}
+
+// Arc (v, w) of a top-down step from level d, sv = sigma[v]: w joins level d+1 unless an
+// earlier level holds it; the lane whose atomicOr sets w's bit in the level-(d+1) bitmap
+// claims and queues it; every such arc adds sigma[v] to sigma[w].
 __device__ __forceinline__ void td_arc(const SrcArgs &a, int d, int w, unsigned long long sv,
                                        int qnext, unsigned long long *s_mf, bool &ovf)
 {
-    int dw = dev::ldcg(a.dist + w);
-    bool claim = false;
-    if (dw < 0) {
-        const int old = atomicCAS(a.dist + w, -1, d + 1);
-        claim = old < 0;
-        dw = claim ? d + 1 : old;
-    }
-    if (dw == d + 1) {
-        const unsigned long long old = atomicAdd(a.sp + w, sv);
-        ovf |= old + sv < old;
-    }
-    if (claim) {
-        cg::coalesced_group g = cg::coalesced_threads();
-        int pos = 0;
-        if (g.thread_rank() == 0) pos = atomicAdd(a.cnt + d + 1, (int)g.size());
-        pos = g.shfl(pos, 0) + (int)g.thread_rank();
-        a.queue[qnext + pos] = w;
+    if (test_bit(vis_bits(a), w)) return;
+    const unsigned bit = 1u << (w & 31);
+    const unsigned old = atomicOr(lvl_bits(a, d + 1) + (w >> 5), bit);
+    if (!(old & bit)) {
+        a.dist[w] = d + 1;
+        queue_append(a, d, qnext, w);
         atomicAdd(s_mf, (unsigned long long)degree(a.rp, w));
     }
+    const unsigned long long prev = atomicAdd(a.sp + w, sv);
+    ovf |= prev + sv < prev;
+}
+
+// fn(j, c) for every arc j of [j0, j1) with c = col[j], by the whole warp: a scalar head
+// up to a 16-byte boundary, then 16-byte column loads (four arcs per lane), then a
+// scalar tail.
+template <class Fn> __device__ __forceinline__ void for_arcs_vec(const SrcArgs &a, int j0, int j1, Fn fn)
+{
+    const int lane = threadIdx.x & 31;
+    const int b0 = min(j1, (j0 + 3) & ~3), b1 = max(b0, j1 & ~3);
+    if (j0 + lane < b0) fn(j0 + lane, __ldg(a.col + j0 + lane));
+    for (int q = b0 / 4 + lane; q < b1 / 4; q += 32) {
+        const int4 c4 = __ldg(reinterpret_cast<const int4 *>(a.col) + q);
+        fn(4 * q, c4.x);
+        fn(4 * q + 1, c4.y);
+        fn(4 * q + 2, c4.z);
+        fn(4 * q + 3, c4.w);
+    }
+    if (b1 + lane < j1) fn(b1 + lane, __ldg(a.col + b1 + lane));
 }
 
 // ------------------------------------------------------------------ top-down level d
-template <int TPV>
-__device__ void td_level(const SrcArgs &a, int d, int qo, int nf, int qnext,
-                         unsigned long long *s_mf, bool &ovf)
+// Light frontier vertices: a warp takes 32 queue entries, stages (v, sigma[v], row
+// start, arcs before it) in shared memory and runs its lanes over the concatenated arcs;
+// the lane of arc i finds its vertex by binary search over the staged prefix sums.
+struct TdStage {
+    int v[32];
+    int beg[32];
+    int pre[33];
+    unsigned long long sv[32];
+};
+
+__device__ void td_level(const SrcArgs &a, int d, int qo, int nf, int qnext, unsigned long long *s_mf,
+                         bool &ovf, TdStage *stages)
 {
-    constexpr int G = 32 / TPV;
-    const Lanes<TPV> L;
-    const long long count = qo >= 0 ? nf : a.n;
-    for (long long base = L.wid * G; base < count; base += L.nw * G) {
-        const long long item = base + L.gw;
-        int v = -1;
-        if (item < count) {
-            if (qo >= 0) v = dev::ldcg(a.queue + qo + item);
-            else if (dev::ldcg(a.dist + item) == d) v = (int)item;
+    const int lane = threadIdx.x & 31;
+    TdStage &st = stages[threadIdx.x >> 5];
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long base = wid * 32; base < nf; base += nwarps * 32) {
+        int v = -1, deg = 0;
+        if (base + lane < nf) {
+            v = __ldcg(a.queue + qo + base + lane);
+            if ((unsigned)v < (unsigned)a.n && !heavy(a, v)) deg = degree(a.rp, v);
+            else v = -1;
         }
-        if (v < 0 || heavy(a, v)) continue;
-        const unsigned long long sv = dev::ldcg(a.sp + v);
-        const int beg = __ldg(a.rp + v), end = __ldg(a.rp + v + 1);
-        for (int j = beg + L.lg; j < end; j += TPV) td_arc(a, d, __ldg(a.col + j), sv, qnext, s_mf, ovf);
+        int incl = deg;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        st.v[lane] = v;
+        st.beg[lane] = v >= 0 ? __ldg(a.rp + v) : 0;
+        st.pre[lane + 1] = incl;
+        st.sv[lane] = v >= 0 ? __ldcg(a.sp + v) : 0ull;
+        if (lane == 0) st.pre[0] = 0;
+        __syncwarp();
+        const int total = __shfl_sync(FULL, incl, 31);
+        for (int i = lane; i < total; i += 32) {
+            int lo = 0, hi = 31;  // last k with pre[k] <= i
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (st.pre[mid] <= i) lo = mid; else hi = mid - 1;
+            }
+            const int j = st.beg[lo] + (i - st.pre[lo]);
+            td_arc(a, d, __ldg(a.col + j), st.sv[lo], qnext, s_mf, ovf);
+        }
+        __syncwarp();
     }
     // heavy frontier vertices: one warp per chunk of kHeavyChunk arcs
-    for (long long c = L.wid; c < a.C; c += L.nw) {
+    for (long long c = wid; c < a.C; c += nwarps) {
         int h, j0, j1;
         chunk_of(a, c, h, j0, j1);
-        if (dev::ldcg(a.dist + h) != d) continue;
-        const unsigned long long sv = dev::ldcg(a.sp + h);
-        for (int j = j0 + L.lane; j < j1; j += 32) td_arc(a, d, __ldg(a.col + j), sv, qnext, s_mf, ovf);
+        if (__ldcg(a.dist + h) != d) continue;
+        const unsigned long long sv = __ldcg(a.sp + h);
+        for_arcs_vec(a, j0, j1, [&](int, int w) { td_arc(a, d, w, sv, qnext, s_mf, ovf); });
     }
 }
 
 // ------------------------------------------------------------------ bottom-up level d
+// Vertex w joins level d+1 with path count acc: distance, sigma, bitmaps, queue, counts.
+__device__ __forceinline__ void bu_settle(const SrcArgs &a, int d, int qnext, int w, unsigned long long acc,
+                                          unsigned long long *s_mf)
+{
+    a.dist[w] = d + 1;
+    a.sp[w] = acc;
+    const unsigned bit = 1u << (w & 31);
+    atomicOr(lvl_bits(a, d + 1) + (w >> 5), bit);
+    atomicOr(vis_bits(a) + (w >> 5), bit);  // only w's own group reads w's bit this level
+    queue_append(a, d, qnext, w);
+    atomicAdd(s_mf, (unsigned long long)degree(a.rp, w));
+}
+
 template <int TPV>
-__device__ void bu_level(const SrcArgs &a, int d, int *s_cnt, unsigned long long *s_mf, bool &ovf)
+__device__ void bu_level(const SrcArgs &a, int d, int qnext, unsigned long long *s_mf, bool &ovf)
 {
     constexpr int G = 32 / TPV;
     const Lanes<TPV> L;
+    const unsigned *cur = lvl_bits(a, d);
     for (long long base = L.wid * G; base < a.n; base += L.nw * G) {
         const long long w = base + L.gw;
-        const bool act = w < a.n && dev::ldcg(a.dist + w) < 0 && !heavy(a, (int)w);
+        const bool act = w < a.n && !test_bit(vis_bits(a), (int)w) && !heavy(a, (int)w);
         unsigned long long acc = 0;
-        int beg = 0, end = 0;
         if (act) {
-            beg = __ldg(a.rp + w);
-            end = __ldg(a.rp + w + 1);
+            const int beg = __ldg(a.rp + w), end = __ldg(a.rp + w + 1);
             for (int j = beg + L.lg; j < end; j += TPV) {
                 const int v = __ldg(a.col + j);
-                if (dev::ldcg(a.dist + v) == d) {
-                    const unsigned long long x = dev::ldcg(a.sp + v);
-                    const unsigned long long y = acc + x;
+                if (test_bit(cur, v)) {
+                    const unsigned long long y = acc + __ldcg(a.sp + v);
                     ovf |= y < acc;
                     acc = y;
                 }
             }
         }
         acc = dev::group_sum_u64<TPV>(acc, ovf);
-        if (act && L.lg == 0 && acc != 0) {
-            a.dist[w] = d + 1;
-            a.sp[w] = acc;
-            atomicAdd(s_cnt, 1);
-            atomicAdd(s_mf, (unsigned long long)(end - beg));
-        }
+        if (act && L.lg == 0 && acc != 0) bu_settle(a, d, qnext, (int)w, acc, s_mf);
     }
     // heavy unvisited vertices: per-chunk partial sums (finished by bu_heavy_finish)
     for (long long c = L.wid; c < a.C; c += L.nw) {
         int h, j0, j1;
         chunk_of(a, c, h, j0, j1);
-        if (dev::ldcg(a.dist + h) >= 0) continue;
+        if (test_bit(vis_bits(a), h)) continue;
         unsigned long long acc = 0;
-        for (int j = j0 + L.lane; j < j1; j += 32) {
-            const int v = __ldg(a.col + j);
-            if (dev::ldcg(a.dist + v) == d) {
-                const unsigned long long y = acc + dev::ldcg(a.sp + v);
+        for_arcs_vec(a, j0, j1, [&](int, int v) {
+            if (test_bit(cur, v)) {
+                const unsigned long long y = acc + __ldcg(a.sp + v);
                 ovf |= y < acc;
                 acc = y;
             }
-        }
+        });
         acc = dev::group_sum_u64<32>(acc, ovf);
         if (L.lane == 0) a.part[c] = acc;
     }
 }
 
 // After a barrier: heavy unvisited vertices add their chunk sums in chunk order.
-__device__ void bu_heavy_finish(const SrcArgs &a, int d, int *s_cnt, unsigned long long *s_mf, bool &ovf)
+__device__ void bu_heavy_finish(const SrcArgs &a, int d, int qnext, unsigned long long *s_mf, bool &ovf)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.H;
          i += (long long)gridDim.x * blockDim.x) {
         const int h = __ldg(a.hv + i);
-        if (dev::ldcg(a.dist + h) >= 0) continue;
+        if (test_bit(vis_bits(a), h)) continue;
         unsigned long long acc = 0;
         for (int c = __ldg(a.hfirst + i); c < __ldg(a.hfirst + i + 1); ++c) {
-            const unsigned long long y = acc + dev::ldcg(a.part + c);
+            const unsigned long long y = acc + __ldcg(a.part + c);
             ovf |= y < acc;
             acc = y;
         }
-        if (acc != 0) {
-            a.dist[h] = d + 1;
-            a.sp[h] = acc;
-            atomicAdd(s_cnt, 1);
-            atomicAdd(s_mf, (unsigned long long)degree(a.rp, h));
-        }
+        if (acc != 0) bu_settle(a, d, qnext, h, acc, s_mf);
     }
 }
 
@@ -229,37 +297,37 @@ __device__ void bu_heavy_finish(const SrcArgs &a, int d, int *s_cnt, unsigned lo
 // Level 0 (the source) is finished only for edge betweenness and gets no score.
 __device__ __forceinline__ void finish_vertex(const SrcArgs &a, int v, dev::ff acc, int d)
 {
-    const dev::ff sv = dev::ff_from_u64(dev::ldcg(a.sp + v));
+    const dev::ff sv = dev::ff_from_u64(__ldcg(a.sp + v));
     const dev::ff delta = dev::ff_mul(sv, acc);
     a.sp[v] = dev::ff_pack(dev::ff_add(dev::ff_rcp(sv), acc));
     if (delta.hi != 0.0f && d > 0) a.scores[v] += dev::ff_to_double(delta);
 }
 
 // ------------------------------------------------------------------ backward level d
+// The level bitmap holds level d+1.
 template <int TPV>
 __device__ void back_level(const SrcArgs &a, int d, int qo, int nd)
 {
     constexpr int G = 32 / TPV;
     const Lanes<TPV> L;
-    const long long count = qo >= 0 ? nd : a.n;
-    for (long long base = L.wid * G; base < count; base += L.nw * G) {
+    const unsigned *succ = lvl_bits(a, 0);
+    for (long long base = L.wid * G; base < nd; base += L.nw * G) {
         const long long item = base + L.gw;
         int v = -1;
-        if (item < count) {
-            if (qo >= 0) v = dev::ldcg(a.queue + qo + item);
-            else if (dev::ldcg(a.dist + item) == d) v = (int)item;
-            if (v >= 0 && heavy(a, v)) v = -1;
+        if (item < nd) {
+            v = __ldcg(a.queue + qo + item);
+            if ((unsigned)v >= (unsigned)a.n || heavy(a, v)) v = -1;
         }
         dev::ff acc = dev::ff_zero();
         if (v >= 0) {
             // edge betweenness: the arc (v, w) carries sigma_v * psi_w = sigma_v / sigma_w *
             // (1 + delta_w), read before v's own psi replaces sigma_v
-            const dev::ff sv = a.edge ? dev::ff_from_u64(dev::ldcg(a.sp + v)) : dev::ff_zero();
+            const dev::ff sv = a.edge ? dev::ff_from_u64(__ldcg(a.sp + v)) : dev::ff_zero();
             const int beg = __ldg(a.rp + v), end = __ldg(a.rp + v + 1);
             for (int j = beg + L.lg; j < end; j += TPV) {
                 const int w = __ldg(a.col + j);
-                if (dev::ldcg(a.dist + w) == d + 1) {
-                    const dev::ff psi = dev::ff_unpack(dev::ldcg(a.sp + w));
+                if (test_bit(succ, w)) {
+                    const dev::ff psi = dev::ff_unpack(__ldcg(a.sp + w));
                     acc = dev::ff_add(acc, psi);
                     if (a.edge) a.edge[j] += dev::ff_to_double(dev::ff_mul(sv, psi));
                 }
@@ -272,17 +340,16 @@ __device__ void back_level(const SrcArgs &a, int d, int qo, int nd)
     for (long long c = L.wid; c < a.C; c += L.nw) {
         int h, j0, j1;
         chunk_of(a, c, h, j0, j1);
-        if (dev::ldcg(a.dist + h) != d) continue;
+        if (__ldcg(a.dist + h) != d) continue;
         dev::ff acc = dev::ff_zero();
-        const dev::ff sv = a.edge ? dev::ff_from_u64(dev::ldcg(a.sp + h)) : dev::ff_zero();
-        for (int j = j0 + L.lane; j < j1; j += 32) {
-            const int w = __ldg(a.col + j);
-            if (dev::ldcg(a.dist + w) == d + 1) {
-                const dev::ff psi = dev::ff_unpack(dev::ldcg(a.sp + w));
+        const dev::ff sv = a.edge ? dev::ff_from_u64(__ldcg(a.sp + h)) : dev::ff_zero();
+        for_arcs_vec(a, j0, j1, [&](int j, int w) {
+            if (test_bit(succ, w)) {
+                const dev::ff psi = dev::ff_unpack(__ldcg(a.sp + w));
                 acc = dev::ff_add(acc, psi);
                 if (a.edge) a.edge[j] += dev::ff_to_double(dev::ff_mul(sv, psi));
             }
-        }
+        });
         acc = dev::group_sum_ff<32>(acc);
         if (L.lane == 0) a.part[c] = dev::ff_pack(acc);
     }
@@ -294,19 +361,32 @@ __device__ void back_heavy_finish(const SrcArgs &a, int d)
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.H;
          i += (long long)gridDim.x * blockDim.x) {
         const int h = __ldg(a.hv + i);
-        if (dev::ldcg(a.dist + h) != d) continue;
+        if (__ldcg(a.dist + h) != d) continue;
         dev::ff acc = dev::ff_zero();
         for (int c = __ldg(a.hfirst + i); c < __ldg(a.hfirst + i + 1); ++c)
-            acc = dev::ff_add(acc, dev::ff_unpack(dev::ldcg(a.part + c)));
+            acc = dev::ff_add(acc, dev::ff_unpack(__ldcg(a.part + c)));
         finish_vertex(a, h, acc, d);
+    }
+}
+
+// Sets (or clears) the bit of every vertex of queue[qo, qo + cnt) in bitmap b.
+__device__ void mark_level(const SrcArgs &a, unsigned *b, int qo, int cnt, bool set)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int v = __ldcg(a.queue + qo + i);
+        if ((unsigned)v >= (unsigned)a.n) continue;
+        const unsigned bit = 1u << (v & 31);
+        if (set) atomicOr(b + (v >> 5), bit);
+        else atomicAnd(b + (v >> 5), ~bit);
     }
 }
 
 template <int TPV>
 __global__ void __launch_bounds__(kThreads) k_source(SrcArgs a)
 {
-    __shared__ int s_cnt;
     __shared__ unsigned long long s_mf;
+    __shared__ TdStage stages[kThreads / 32];
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nthr = (long long)gridDim.x * blockDim.x;
     const int s = __ldg(a.src);
@@ -315,6 +395,7 @@ __global__ void __launch_bounds__(kThreads) k_source(SrcArgs a)
         a.dist[v] = v == s ? 0 : -1;
         a.sp[v] = v == s ? 1ull : 0ull;
     }
+    for (long long i = tid; i < 3LL * a.nw; i += nthr) a.bits[i] = 0u;
     if (tid == 0) {
         a.queue[0] = s;
         a.cnt[0] = 1;
@@ -323,47 +404,47 @@ __global__ void __launch_bounds__(kThreads) k_source(SrcArgs a)
         a.qoff[0] = 0;
     }
     if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+    if (tid == 0) {
+        atomicOr(vis_bits(a) + (s >> 5), 1u << (s & 31));
+        atomicOr(lvl_bits(a, 0) + (s >> 5), 1u << (s & 31));
+    }
+    if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
     const int deg_s = degree(a.rp, s);
     long long mu = a.A - deg_s, mf = deg_s;
-    int d = 0, qo = 0, nf = 1, qtail = 1, td = 0, bu = 0;
+    int d = 0, qo = 0, nf = 1, td = 0, bu = 0;
     for (;;) {
-        if (threadIdx.x == 0) {
-            s_cnt = 0;
-            s_mf = 0;
-        }
+        const int qnext = qo + nf;  // level d+1 starts after level d in the queue
+        if (threadIdx.x == 0) s_mf = 0;
         if (tid == 0) {
             a.cnt[d + 2] = 0;  // used by level d+1
             a.mfa[d + 2] = 0;
+            a.qoff[d + 1] = qnext;
         }
         __syncthreads();
         const bool use_bu = a.dir == NK_DIR_BOTTOM_UP ||
                             (a.dir == NK_DIR_AUTO && a.alpha * (double)mf > (double)mu);
         if (use_bu) {
-            bu_level<TPV>(a, d, &s_cnt, &s_mf, ovf);
+            bu_level<TPV>(a, d, qnext, &s_mf, ovf);
             if (a.H > 0) {
                 if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
-                bu_heavy_finish(a, d, &s_cnt, &s_mf, ovf);
+                bu_heavy_finish(a, d, qnext, &s_mf, ovf);
             }
         } else {
-            td_level<TPV>(a, d, qo, nf, qtail, &s_mf, ovf);
+            td_level(a, d, qo, nf, qnext, &s_mf, ovf, stages);
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            if (s_cnt) atomicAdd(a.cnt + d + 1, s_cnt);
-            if (s_mf) atomicAdd((unsigned long long *)(a.mfa + d + 1), (unsigned long long)s_mf);
-        }
-        if (tid == 0) a.qoff[d + 1] = use_bu ? -1 : qtail;
+        if (threadIdx.x == 0 && s_mf) atomicAdd((unsigned long long *)(a.mfa + d + 1), (unsigned long long)s_mf);
         if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
-        const int c = dev::ldcg(a.cnt + d + 1);
-        const long long m2 = dev::ldcg(a.mfa + d + 1);
-        if (use_bu) {
-            ++bu;
-            qo = -1;
-        } else {
-            ++td;
-            qo = qtail;
-            qtail += c;
-        }
+        // level d+1 is complete: a top-down level adds it to vis (bottom-up set the bits as
+        // it settled), and level d's bits leave its level bitmap for use by level d+2
+        const int c = __ldcg(a.cnt + d + 1);
+        if (!use_bu) mark_level(a, vis_bits(a), qnext, c, true);
+        mark_level(a, lvl_bits(a, d), qo, nf, false);
+        if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+        const long long m2 = __ldcg(a.mfa + d + 1);
+        if (use_bu) ++bu;
+        else ++td;
+        qo = qnext;
         nf = c;
         mu -= m2;
         mf = m2;
@@ -378,9 +459,14 @@ __global__ void __launch_bounds__(kThreads) k_source(SrcArgs a)
     }
     if (ovf) atomicOr(&a.ctrl->ovf, 1);
     if (a.forward_only) return;
-    // edge betweenness also sweeps level 0: the source's arcs carry shares
+    // the level bitmaps are empty again; level bitmap 0 holds level l+1 while level l is
+    // swept (edge betweenness also sweeps level 0: the source's arcs carry shares)
     for (int l = D; l >= (a.edge ? 0 : 1); --l) {
-        back_level<TPV>(a, l, dev::ldcg(a.qoff + l), dev::ldcg(a.cnt + l));
+        const int ql = __ldcg(a.qoff + l), nl = __ldcg(a.cnt + l);
+        if (l + 2 <= D) mark_level(a, lvl_bits(a, 0), __ldcg(a.qoff + l + 2), __ldcg(a.cnt + l + 2), false);
+        if (l + 1 <= D) mark_level(a, lvl_bits(a, 0), __ldcg(a.qoff + l + 1), __ldcg(a.cnt + l + 1), true);
+        if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+        back_level<TPV>(a, l, ql, nl);
         if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
         if (a.H > 0) {
             back_heavy_finish(a, l);
@@ -504,7 +590,8 @@ int run(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores, const Ru
     NK_TRY(ws[WS_SP].ensure(sizeof(uint64_t) * n));
     NK_TRY(ws[WS_QUEUE].ensure(sizeof(int32_t) * n));
     const size_t lv = (size_t)n + 3;
-    NK_TRY(ws[WS_LEVELS].ensure(lv * (sizeof(int32_t) * 2 + sizeof(long long))));
+    const int32_t nw = (n + 31) / 32;
+    NK_TRY(ws[WS_LEVELS].ensure(lv * (sizeof(int32_t) * 2 + sizeof(long long)) + 3 * sizeof(unsigned) * (size_t)nw));
     NK_TRY(ws[WS_CTRL].ensure(sizeof(Ctrl)));
     NK_TRY(build_heavy(g, s));
     NK_TRY(ws[WS_PART].ensure(sizeof(unsigned long long) * std::max<int64_t>(g->heavy_C, 1)));
@@ -524,6 +611,8 @@ int run(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores, const Ru
     a.mfa = reinterpret_cast<long long *>(lvb);
     a.cnt = reinterpret_cast<int32_t *>(lvb + lv * sizeof(long long));
     a.qoff = a.cnt + lv;
+    a.bits = reinterpret_cast<unsigned *>(a.qoff + lv);
+    a.nw = nw;
     a.scores = d_scores;
     a.ctrl = ws[WS_CTRL].as<Ctrl>();
     a.limit_ns = cfg.limit_ns ? cfg.limit_ns : wait_limit_ns();
@@ -626,7 +715,7 @@ int run_sssp(nk_graph *g, int32_t src, int32_t *d_dist, uint64_t *d_sigma, cudaS
 // A variant of the forward sweep for callers that cannot allocate device memory at
 // call time (for example code running under an allocator that forbids cudaMalloc, or
 // a host library that must not grow its footprint once started).  Its scratch - the
-// control block, the BFS queue and the per-level counters - lives in one file-scope
+// control block, the BFS queue, the per-level counters and the frontier bitmaps - lives in one file-scope
 // device array of fixed size, so the call allocates nothing; inputs (the CSR) and
 // outputs (dist, sigma) are the caller's device buffers.  Rows are not split into
 // chunks here (the chunk table would need an allocation), so a high-degree vertex is
@@ -643,7 +732,8 @@ constexpr size_t kNaQueue = 512;
 constexpr size_t kNaCnt = na_align(kNaQueue + 4 * (size_t)kNoAllocMaxN);
 constexpr size_t kNaQoff = na_align(kNaCnt + 4 * kNaLv);
 constexpr size_t kNaMfa = na_align(kNaQoff + 4 * kNaLv);
-constexpr size_t kNaPart = na_align(kNaMfa + 8 * kNaLv);
+constexpr size_t kNaBits = na_align(kNaMfa + 8 * kNaLv);
+constexpr size_t kNaPart = na_align(kNaBits + 3 * sizeof(unsigned) * (size_t)(kNoAllocMaxN / 32));
 constexpr size_t kNaBytes = kNaPart + 256;
 
 }  // namespace
@@ -719,6 +809,8 @@ extern "C" int nk_sssp_noalloc(int32_t n, const int32_t *row_ptr, const int32_t 
     a.H = 0;
     a.C = 0;
     a.part = reinterpret_cast<unsigned long long *>(scr + kNaPart);
+    a.bits = reinterpret_cast<unsigned *>(scr + kNaBits);
+    a.nw = (n + 31) / 32;
     a.edge = nullptr;
     // the control block keeps the previous call's words: it must start at zero
     NK_CUDA(cudaMemsetAsync(a.ctrl, 0, sizeof(Ctrl), st));

@@ -59,6 +59,15 @@ def hypercube(d):
     return _edges(n, ((x, x ^ (1 << b)) for x in range(n) for b in range(d) if x < x ^ (1 << b)))
 
 
+def hypercube_edges(d):
+    """Edge list (u < v) of the hypercube Q_d built with numpy (for large d)."""
+    n = 1 << d
+    x = np.repeat(np.arange(n, dtype=np.int64), d)
+    y = x ^ (1 << np.tile(np.arange(d, dtype=np.int64), n))
+    keep = x < y
+    return n, x[keep].astype(np.int32), y[keep].astype(np.int32)
+
+
 def random_tree(n, seed):
     """Vertex i > 0 hangs off a uniformly chosen earlier vertex; ids are then permuted."""
     rng = np.random.default_rng(seed)

@@ -179,6 +179,40 @@ def test_sigma_near_limit_and_overflow(nk):
         assert e.value.rc == nk.ERR_OVERFLOW
 
 
+def _forms(nk):
+    return (nk.run_opts(mode=nk.MODE_PER_SOURCE), nk.run_opts(mode=nk.MODE_BATCHED, batch=64),
+            nk.run_opts(mode=nk.MODE_BATCHED, batch=256))
+
+
+def test_scores_with_sigma_near_the_limit(nk):
+    # 34 x 35 grid: from a corner sigma reaches C(67, 33) ~ 1.42e19 (2^63.6), where the
+    # double-single conversion of sigma and its reciprocal keep about 48 of its 64 bits; the
+    # scores of the four corners and a spread of other sources in the per-source form and in
+    # batches of 64 and 256
+    g, rp, col = both(nk, G.grid(34, 35))
+    n = len(rp) - 1
+    src = np.array([0, 34, 33 * 35, n - 1] + list(range(1, n - 1, 7)), np.int32)
+    _, s0 = oracle.bfs(rp, col, 0)
+    assert int(s0.max()) == 14226520737620288370  # C(67, 33) > 2^63
+    want = oracle.betweenness_sources(rp, col, src, 1.0)
+    for opts in _forms(nk):
+        assert close(nk.betweenness_sources(g, src, 1.0, opts), want), opts.mode
+
+
+def test_scores_on_a_large_hypercube(nk):
+    # Q_20 (2^20 vertices, 20 arcs each): sigma from x to its antipode is 20! ~ 2.4e18 (2^61)
+    n, u, v = G.hypercube_edges(20)
+    g = nk.graph_from_edges(n, u, v)
+    rp, col = oracle.csr_build(n, u, v)
+    src = np.array([0, n - 1, 0x55555, 0xAAAAA, 12345, 777777, 3, 1 << 19], np.int32)
+    _, s0 = oracle.bfs(rp, col, 0)
+    assert int(s0[n - 1]) == 2432902008176640000  # 20!
+    want = oracle.betweenness_sources(rp, col, src, 1.0)
+    for opts in _forms(nk):
+        assert close(nk.betweenness_sources(g, src, 1.0, opts), want), opts.mode
+    g.free()
+
+
 # ------------------------------------------------------------------ betweenness
 @pytest.mark.parametrize("name", sorted(SMALL))
 def test_exact_small_graphs(nk, name):
