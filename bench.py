@@ -491,8 +491,15 @@ def extension_legs(nk, torch, g, n, A, m, k, B, opts, stats, sseed, args, flush,
     leg = {"value": m * wk / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms, "k": wk, "wmax": wmax,
            "buckets_max": st["max_depth"],
            "groups": st["batch"], "ctas_per_search": st["tpv"],
-           "roofline": _roof(weighted_bytes(n, A) * wk / max(1, st["launches"]), lms, peak, peak_kind,
-                             "k_wsource (searches side by side in CTA groups)"),
+           # the groups' per-search state (distances, sigma/psi: 16 bytes per vertex and search)
+           # stays in L2, so an HBM fraction would say nothing: the kernel is bound by the latency
+           # of its dependent loads (ncu: DRAM throughput 2.5 %, L2 hit rate 81 %, long-scoreboard
+           # stalls 13.8 per issue); the byte rate of its model is reported for reference
+           "roofline": dict(_roof(weighted_bytes(n, A) * wk / max(1, st["launches"]), lms, peak, peak_kind,
+                                  "k_wsource (searches side by side in CTA groups)"),
+                            bound="latency", peak=None, frac=None, frac_nominal=None,
+                            state_bytes=16 * n * max(1, st["batch"]),
+                            note="per-search state L2-resident; latency-bound, no HBM fraction"),
            "form": "Dijkstra sweeps by distance buckets, one per CTA group, sampled sources, scale n/(2k)"}
     if ora:
         o, rp_o, col_o, src_o = ora
@@ -667,6 +674,12 @@ def run_ours(args, world, rank, local):
                 "algorithmic_bytes_per_launch": alg, "avg_launch_ms": per_launch_ms,
                 "launches_per_step": steps_launches,
                 "model": "per launch (8A + 24n) + 34n x (sources of the launch); sources without arcs are skipped"}
+    if traffic:
+        # the DRAM bytes ncu counts per launch, over this run's average launch: the HBM rate the
+        # kernel actually drives (its gathers re-read rows, so traffic exceeds the model)
+        roofline["traffic_gbs"] = traffic / (per_launch_ms / 1e3) / 1e9
+        roofline["traffic_frac"] = roofline["traffic_gbs"] / peak
+        roofline["traffic_over_model"] = traffic / alg
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,

@@ -163,7 +163,8 @@ int nk_sssp_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col, int64
 typedef struct nk_run_opts {
     int32_t mode;      /* NK_MODE_* */
     int32_t batch;     /* batched mode: sources per batch, 64/128/256; 0 = autotuned */
-    int32_t tpv;       /* per-source mode: threads per vertex 1..32 (power of 2); 0 = auto */
+    int32_t tpv;       /* accepted for compatibility (0 or a power of 2 <= 32) and ignored: the
+                          per-source sweep runs lanes over the arcs of groups of vertices */
     int32_t direction; /* NK_DIR_* */
     double alpha;      /* bottom-up when alpha * (frontier arcs) > (unvisited arcs); 0 = auto */
     uint32_t flags;    /* NK_RUN_* */

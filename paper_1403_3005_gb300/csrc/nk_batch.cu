@@ -50,6 +50,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kErrDepth = 100;  // internal status: BFS deeper than the level slabs
 constexpr int kErrCheck = 101;  // internal status: a device-side range check failed
+constexpr int kErrWide = 102;   // internal status: a path count did not fit the 32-bit sigma rows
 constexpr int kStartLevels = 48; // level slabs of a first attempt
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int kTraceCap = 1024;
@@ -74,6 +75,7 @@ struct BArgs {
     unsigned long long *F;       // [lcap+2][n][W]
     unsigned long long *vis;     // [n][W]
     unsigned long long *sp;      // [n][B]
+    unsigned *sp32;              // [n][B] sigma in 32 bits during the forward sweep (kernels with S32)
     int32_t *qmark;              // [n] last level a vertex was queued for
     int32_t *queue;              // [qcap]
     int64_t qcap;
@@ -217,7 +219,7 @@ template <int W> struct Nbrs {
 // share sum_b sigma_b(v) * psi_b(c) over the gathered source bits (sv holds sigma_b(v) of
 // the lane's slots): a warp sum per neighbour, added to edge[j] by lane 0.  The arc is
 // owned by v's warp at this level, so no atomics are needed.
-template <int W, bool PSI, bool EDGE = false>
+template <int W, bool PSI, bool EDGE = false, bool S32 = false>
 __device__ __forceinline__ void gather(const BArgs &a, int beg, int end,
                                        const unsigned long long *Fsel, const Bits<W> &tgt,
                                        unsigned long long (&acc)[2 * W], dev::ff (&facc)[2 * W],
@@ -271,12 +273,21 @@ __device__ __forceinline__ void gather(const BArgs &a, int beg, int end,
             unsigned pb[NB][W];
 #pragma unroll
             for (int r = 0; r < NB; ++r) {
-                const unsigned long long *row = a.sp + (size_t)st.c[idx[r]] * B + 2 * lane;
 #pragma unroll
                 for (int q = 0; q < W; ++q) {
                     pb[r][q] = on[r] ? pair_bits<W>(st.f[idx[r]][q], lane) : 0u;
                     v[r][q] = make_ulonglong2(0ull, 0ull);
-                    if (pb[r][q]) v[r][q] = __ldcg(reinterpret_cast<const ulonglong2 *>(row + 64 * q));
+                    if constexpr (S32) {
+                        // 32-bit sigma rows: one 8-byte load holds the lane's pair
+                        const unsigned *row = a.sp32 + (size_t)st.c[idx[r]] * B + 2 * lane;
+                        if (pb[r][q]) {
+                            const unsigned long long p = __ldcg(reinterpret_cast<const unsigned long long *>(row + 64 * q));
+                            v[r][q] = make_ulonglong2(p & 0xffffffffull, p >> 32);
+                        }
+                    } else {
+                        const unsigned long long *row = a.sp + (size_t)st.c[idx[r]] * B + 2 * lane;
+                        if (pb[r][q]) v[r][q] = __ldcg(reinterpret_cast<const ulonglong2 *>(row + 64 * q));
+                    }
                 }
             }
             unsigned long long x[NB][2 * W];
@@ -349,17 +360,30 @@ struct BlockCnt {
 // Vertex w joined level d+1 for the sources in nb (vold = its visited set before):
 // writes its sigma row and visited set (and F_{d+1} when Fn is given), and counts it.
 // Called by the whole warp with warp-uniform arguments.
-template <int W>
+template <int W, bool S32 = false>
 __device__ __forceinline__ void settle(const BArgs &a, int w, const Bits<W> &vold, const Bits<W> &nb,
                                        const Bits<W> &act, const unsigned long long (&acc)[2 * W],
                                        unsigned long long *Fn, BlockCnt *bc)
 {
     constexpr int B = 64 * W;
     const int lane = threadIdx.x & 31;
-    unsigned long long *row = a.sp + (size_t)w * B;
+    if constexpr (S32) {
+        // a count that does not fit 32 bits sends the batch back to the 64-bit kernel
+        unsigned *row = a.sp32 + (size_t)w * B;
+        bool wide = false;
 #pragma unroll
-    for (int k = 0; k < 2 * W; ++k)
-        if (has_slot<W>(nb, k, lane)) row[slot_off(k, lane)] = acc[k];
+        for (int k = 0; k < 2 * W; ++k)
+            if (has_slot<W>(nb, k, lane)) {
+                row[slot_off(k, lane)] = (unsigned)acc[k];
+                wide |= (acc[k] >> 32) != 0;
+            }
+        if (wide) atomicCAS(&a.ctrl->err, 0, kErrWide);
+    } else {
+        unsigned long long *row = a.sp + (size_t)w * B;
+#pragma unroll
+        for (int k = 0; k < 2 * W; ++k)
+            if (has_slot<W>(nb, k, lane)) row[slot_off(k, lane)] = acc[k];
+    }
     bool full = true;
 #pragma unroll
     for (int q = 0; q < W; ++q) {
@@ -522,7 +546,7 @@ __device__ __forceinline__ void store_part(const BArgs &a, int c, const unsigned
 
 __device__ __forceinline__ bool heavy(const BArgs &a, int v) { return deg_of(a.rp, v) > a.chunk; }
 
-template <int W, bool EDGE>
+template <int W, bool EDGE, bool S32>
 __global__ void __launch_bounds__(kThreads, (W <= 2 ? 4 : 2)) k_batch(BArgs a)
 {
     constexpr int B = 64 * W;
@@ -575,7 +599,8 @@ __global__ void __launch_bounds__(kThreads, (W <= 2 ? 4 : 2)) k_batch(BArgs a)
         const unsigned long long bit = 1ull << (tid & 63);
         atomicOr(a.F + (size_t)s * W + (tid >> 6), bit);
         atomicOr(a.vis + (size_t)s * W + (tid >> 6), bit);
-        a.sp[(size_t)s * B + tid] = 1ull;
+        if constexpr (S32) a.sp32[(size_t)s * B + tid] = 1u;
+        else a.sp[(size_t)s * B + tid] = 1ull;
         a.queue[tid] = s;
         atomicAdd(a.mfv, (unsigned long long)deg_of(a.rp, s));
         if (nsrc == 1) a.dmu[0] = (unsigned long long)deg_of(a.rp, s);
@@ -644,9 +669,9 @@ __global__ void __launch_bounds__(kThreads, (W <= 2 ? 4 : 2)) k_batch(BArgs a)
                     dev::ff facc[2 * W];
 #pragma unroll
                     for (int k = 0; k < 2 * W; ++k) acc[k] = 0;
-                    gather<W, false>(a, __ldg(a.rp + w), __ldg(a.rp + w + 1), Fd, u, acc, facc, ovf, st);
+                    gather<W, false, false, S32>(a, __ldg(a.rp + w), __ldg(a.rp + w + 1), Fd, u, acc, facc, ovf, st);
                     const Bits<W> nb = nonzero_bits<W>(acc);
-                    if (any_bits<W>(nb)) settle<W>(a, w, vold, nb, act, acc, Fn, &bc);
+                    if (any_bits<W>(nb)) settle<W, S32>(a, w, vold, nb, act, acc, Fn, &bc);
                 }
             }
             for_chunks(a, a.wq + (size_t)d * 8 + WQ_BU_C, [&](int c, int h, int j0, int j1) {
@@ -656,7 +681,7 @@ __global__ void __launch_bounds__(kThreads, (W <= 2 ? 4 : 2)) k_batch(BArgs a)
                 dev::ff facc[2 * W];
 #pragma unroll
                 for (int k = 0; k < 2 * W; ++k) acc[k] = 0;
-                gather<W, false>(a, j0, j1, Fd, u, acc, facc, ovf, st);
+                gather<W, false, false, S32>(a, j0, j1, Fd, u, acc, facc, ovf, st);
                 store_part<W>(a, c, acc);
             });
             if (a.H > 0 && !dev::grid_barrier(a.ctrl, a.limit_ns)) return;
@@ -678,7 +703,7 @@ __global__ void __launch_bounds__(kThreads, (W <= 2 ? 4 : 2)) k_batch(BArgs a)
                     }
                 }
                 const Bits<W> nb = nonzero_bits<W>(acc);
-                if (any_bits<W>(nb)) settle<W>(a, h, vold, nb, act, acc, Fn, &bc);
+                if (any_bits<W>(nb)) settle<W, S32>(a, h, vold, nb, act, acc, Fn, &bc);
             });
             flush_counts(d + 1);
             if (tid == 0) a.qoff[d + 1] = -1;
@@ -725,8 +750,8 @@ __global__ void __launch_bounds__(kThreads, (W <= 2 ? 4 : 2)) k_batch(BArgs a)
                 dev::ff facc[2 * W];
 #pragma unroll
                 for (int k = 0; k < 2 * W; ++k) acc[k] = 0;
-                gather<W, false>(a, __ldg(a.rp + w), __ldg(a.rp + w + 1), Fd, t, acc, facc, ovf, st);
-                settle<W>(a, w, vold, t, act, acc, nullptr, &bc);
+                gather<W, false, false, S32>(a, __ldg(a.rp + w), __ldg(a.rp + w + 1), Fd, t, acc, facc, ovf, st);
+                settle<W, S32>(a, w, vold, t, act, acc, nullptr, &bc);
             });
             for_chunks(a, a.wq + (size_t)d * 8 + WQ_PULL_C, [&](int c, int h, int j0, int j1) {
                 const Bits<W> t = load_bits<W>(Fn + (size_t)h * W);
@@ -735,7 +760,7 @@ __global__ void __launch_bounds__(kThreads, (W <= 2 ? 4 : 2)) k_batch(BArgs a)
                 dev::ff facc[2 * W];
 #pragma unroll
                 for (int k = 0; k < 2 * W; ++k) acc[k] = 0;
-                gather<W, false>(a, j0, j1, Fd, t, acc, facc, ovf, st);
+                gather<W, false, false, S32>(a, j0, j1, Fd, t, acc, facc, ovf, st);
                 store_part<W>(a, c, acc);
             });
             if (a.H > 0 && !dev::grid_barrier(a.ctrl, a.limit_ns)) return;
@@ -757,7 +782,7 @@ __global__ void __launch_bounds__(kThreads, (W <= 2 ? 4 : 2)) k_batch(BArgs a)
                         acc[k] = y;
                     }
                 }
-                settle<W>(a, h, vold, t, act, acc, nullptr, &bc);
+                settle<W, S32>(a, h, vold, t, act, acc, nullptr, &bc);
             });
             flush_counts(d + 1);
             if (tid == 0) a.qoff[d + 1] = queued ? (int)qtail : -1;
@@ -814,7 +839,8 @@ __global__ void __launch_bounds__(kThreads, (W <= 2 ? 4 : 2)) k_batch(BArgs a)
             const unsigned long long key = __ldg(a.rk_key + b);
             int w = v;
             for (int l = L, step = 0; l > 1; --l, ++step) {
-                const unsigned long long sw = __ldcg(a.sp + (size_t)w * B + b);
+                const unsigned long long sw = S32 ? (unsigned long long)__ldcg(a.sp32 + (size_t)w * B + b)
+                                                  : __ldcg(a.sp + (size_t)w * B + b);
                 const unsigned long long t = dev::below(dev::stream_at(key, (uint64_t)step), sw);
                 const unsigned long long *Fp = a.F + (size_t)(l - 1) * slab;
                 const int end = __ldg(a.rp + w + 1);
@@ -826,7 +852,8 @@ __global__ void __launch_bounds__(kThreads, (W <= 2 ? 4 : 2)) k_batch(BArgs a)
                     unsigned long long x = 0;
                     if (j < end) {
                         c = __ldg(a.col + j);
-                        if (__ldcg(Fp + (size_t)c * W + q) & bit) x = __ldcg(a.sp + (size_t)c * B + b);
+                        if (__ldcg(Fp + (size_t)c * W + q) & bit)
+                            x = S32 ? (unsigned long long)__ldcg(a.sp32 + (size_t)c * B + b) : __ldcg(a.sp + (size_t)c * B + b);
                     }
                     unsigned long long incl = x;  // inclusive prefix over the lanes
 #pragma unroll
@@ -887,7 +914,9 @@ __global__ void __launch_bounds__(kThreads, (W <= 2 ? 4 : 2)) k_batch(BArgs a)
 #pragma unroll
             for (int k = 0; k < 2 * W; ++k) {
                 if (has_slot<W>(mv, k, lane)) {
-                    const dev::ff sv = dev::ff_from_u64(__ldcg(row + slot_off(k, lane)));
+                    const unsigned long long sg = S32 ? (unsigned long long)__ldcg(a.sp32 + (size_t)v * B + slot_off(k, lane))
+                                                      : __ldcg(row + slot_off(k, lane));
+                    const dev::ff sv = dev::ff_from_u64(sg);
                     const dev::ff delta = dev::ff_mul(sv, facc[k]);
                     row[slot_off(k, lane)] = dev::ff_pack(dev::ff_add(dev::ff_rcp(sv), facc[k]));
                     part = dev::ff_add(part, delta);
@@ -956,13 +985,13 @@ template <int W> constexpr size_t smem_bytes() { return (size_t)(kThreads / 32) 
 
 // Co-resident CTAs per SM of k_batch<W, EDGE> with its shared memory (the shared-memory
 // attribute is set on the first call, outside any stream capture).
-template <int W, bool EDGE = false> int blocks_per_sm()
+template <int W, bool EDGE = false, bool S32 = false> int blocks_per_sm()
 {
     static int b = -1;
     if (b < 0) {
-        NK_CUDA(cudaFuncSetAttribute(k_batch<W, EDGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<W>()));
+        NK_CUDA(cudaFuncSetAttribute(k_batch<W, EDGE, S32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<W>()));
         int v = 0;
-        NK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_batch<W, EDGE>, kThreads, smem_bytes<W>()));
+        NK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_batch<W, EDGE, S32>, kThreads, smem_bytes<W>()));
         b = v;
     }
     return b;
@@ -971,7 +1000,7 @@ template <int W, bool EDGE = false> int blocks_per_sm()
 struct Layout {
     int W, B, lcap;
     int64_t qcap;
-    size_t off_F, off_vis, off_sp, off_qmark, off_queue, off_cnt, off_part, total;
+    size_t off_F, off_vis, off_sp, off_sp32, off_qmark, off_queue, off_cnt, off_part, total;
 };
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -1001,6 +1030,8 @@ Layout layout(const nk_graph *g, int B, int lcap, int chunk = 0)
     o = align_up(o + n * L.W * 8);
     L.off_sp = o;
     o = align_up(o + n * (size_t)B * 8);
+    L.off_sp32 = o;
+    o = align_up(o + n * (size_t)B * 4);
     L.off_qmark = o;
     o = align_up(o + n * 4);
     L.off_queue = o;
@@ -1067,11 +1098,22 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
     const int nb = (k + B - 1) / B;
     NK_TRY(ws[WS_BCTRL].ensure(sizeof(Ctrl) * nb));
     const bool edge = cfg.edge && cfg.backward;
-    const int bps = edge ? blocks_per_sm<W, true>() : blocks_per_sm<W>();
-    if (bps < 1) return set_error(NK_ERR_CUDA, "batched kernel cannot be resident");
-    const void *kfn = edge ? (const void *)k_batch<W, true> : (const void *)k_batch<W, false>;
-    int grid = std::max(1, bps * num_sms() / std::max(1, cfg.grid_div));
-    if (cfg.grid_ctas > 0) grid = std::min(grid, cfg.grid_ctas);
+    // sigma in 32-bit rows unless a batch's counts do not fit (then that batch is rerun with
+    // 64-bit rows); the edge variant keeps 64-bit rows
+    bool s32 = !edge;
+    auto pick = [&](const void *&kfn, int &grid) -> int {
+        const int bps = edge ? blocks_per_sm<W, true, false>() : s32 ? blocks_per_sm<W, false, true>()
+                                                                     : blocks_per_sm<W, false, false>();
+        if (bps < 1) return set_error(NK_ERR_CUDA, "batched kernel cannot be resident");
+        kfn = edge ? (const void *)k_batch<W, true, false>
+                   : s32 ? (const void *)k_batch<W, false, true> : (const void *)k_batch<W, false, false>;
+        grid = std::max(1, bps * num_sms() / std::max(1, cfg.grid_div));
+        if (cfg.grid_ctas > 0) grid = std::min(grid, cfg.grid_ctas);
+        return NK_OK;
+    };
+    const void *kfn = nullptr;
+    int grid = 0;
+    NK_TRY(pick(kfn, grid));
     Ctrl *ctrls = ws[WS_BCTRL].as<Ctrl>();
     std::vector<int> todo(nb);
     for (int bi = 0; bi < nb; ++bi) todo[bi] = bi;
@@ -1095,6 +1137,8 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
         a.F = reinterpret_cast<unsigned long long *>(base + L.off_F);
         a.vis = reinterpret_cast<unsigned long long *>(base + L.off_vis);
         a.sp = reinterpret_cast<unsigned long long *>(base + L.off_sp);
+    a.sp32 = reinterpret_cast<unsigned *>(base + L.off_sp32);
+        a.sp32 = reinterpret_cast<unsigned *>(base + L.off_sp32);
         a.qmark = reinterpret_cast<int32_t *>(base + L.off_qmark);
         a.queue = reinterpret_cast<int32_t *>(base + L.off_queue);
         a.qcap = L.qcap;
@@ -1176,7 +1220,29 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
                         names[std::min<unsigned long long>(t[2 * i] % 16, 8)], (t[2 * i + 1] - t[2 * i - 1]) * 1e-3);
         }
         bool ovf = false;
-        std::vector<int> deep;
+        std::vector<int> deep, wide;
+        for (int bi : todo) {
+            if (h[bi].err == NK_ERR_TIMEOUT)
+                return set_error(NK_ERR_TIMEOUT, "batched sweep aborted: a bounded device-side wait or phase ran out (check %d, value %d)",
+                                 h[bi].where, h[bi].bad_id);
+            if (h[bi].err == kErrCheck)
+                return set_error(NK_ERR_CUDA, "batched sweep aborted: device range check %d failed (value %d)",
+                                 h[bi].where, h[bi].bad_id);
+        }
+        for (int bi : todo)
+            if (h[bi].err == kErrWide) wide.push_back(bi);
+        if (!wide.empty()) {
+            // counts beyond 32 bits: these batches again with 64-bit sigma rows, together with
+            // any that ran out of level slabs (an aborted batch never reaches the backward
+            // sweep, so it has added nothing to the scores)
+            for (int bi : todo)
+                if (h[bi].err == kErrDepth) wide.push_back(bi);
+            std::sort(wide.begin(), wide.end());
+            s32 = false;
+            NK_TRY(pick(kfn, grid));
+            todo = wide;
+            continue;
+        }
         for (int bi : todo) {
             if (h[bi].err == NK_ERR_TIMEOUT)
                 return set_error(NK_ERR_TIMEOUT, "batched sweep aborted: a bounded device-side wait or phase ran out (check %d, value %d)",
@@ -1234,12 +1300,12 @@ int enqueue_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scor
     if (prepare_only) {
         NK_TRY(ws[WS_BATCH].ensure(L.total));
         NK_TRY(ws[WS_BCTRL].ensure(bctrl_bytes));
-        if (blocks_per_sm<W>() < 1) return set_error(NK_ERR_CUDA, "batched kernel cannot be resident");
+        if (blocks_per_sm<W, false, true>() < 1) return set_error(NK_ERR_CUDA, "batched kernel cannot be resident");
         return NK_OK;
     }
     if (ws[WS_BATCH].bytes < L.total || ws[WS_BCTRL].bytes < bctrl_bytes)
         return set_error(NK_ERR_ARG, "batched workspace not prepared");
-    const int bps = blocks_per_sm<W>();
+    const int bps = blocks_per_sm<W, false, true>();
     if (bps < 1) return set_error(NK_ERR_CUDA, "batched kernel cannot be resident");
     int grid = std::max(1, bps * num_sms() / std::max(1, cfg.grid_div));
     if (cfg.grid_ctas > 0) grid = std::min(grid, cfg.grid_ctas);
@@ -1253,6 +1319,7 @@ int enqueue_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scor
     a.F = reinterpret_cast<unsigned long long *>(base + L.off_F);
     a.vis = reinterpret_cast<unsigned long long *>(base + L.off_vis);
     a.sp = reinterpret_cast<unsigned long long *>(base + L.off_sp);
+    a.sp32 = reinterpret_cast<unsigned *>(base + L.off_sp32);
     a.qmark = reinterpret_cast<int32_t *>(base + L.off_qmark);
     a.queue = reinterpret_cast<int32_t *>(base + L.off_queue);
     a.qcap = L.qcap;
@@ -1306,7 +1373,7 @@ int enqueue_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scor
         a.boff = bi * B;
         a.ctrl = ctrls + bi;
         void *args[] = {&a};
-        NK_CUDA(cudaLaunchKernelExC(&lc, (const void *)k_batch<W, false>, args));
+        NK_CUDA(cudaLaunchKernelExC(&lc, (const void *)k_batch<W, false, true>, args));
         ::nk::count_launch();
     }
     *ctrls_out = ctrls;

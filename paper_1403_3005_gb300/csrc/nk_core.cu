@@ -54,12 +54,33 @@ int num_sms()
 }
 
 // ---------------------------------------------------------------- buffers
+// The device's default memory pool, which the stream-ordered allocations of the library
+// draw from, keeps freed memory for reuse instead of returning it to the driver at every
+// synchronisation (its release threshold is raised once per device; the pool belongs to
+// this process).
+static void keep_pool_memory()
+{
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    const unsigned long long bit = 1ull << dev;
+    if (done.load() & bit) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done.fetch_or(bit);
+}
+
 int DevBuf::ensure(size_t b)
 {
     if (b <= bytes && p) return NK_OK;
     release();
     size_t want = b < 256 ? 256 : b;
     count_alloc();
+    if (stream_ordered) keep_pool_memory();
     cudaError_t e = stream_ordered ? cudaMallocAsync(&p, want, st) : cudaMalloc(&p, want);
     if (e != cudaSuccess) {
         p = nullptr;
@@ -85,6 +106,7 @@ int Tmp::alloc(size_t b, cudaStream_t s)
 {
     st = s;
     count_alloc();
+    keep_pool_memory();
     cudaError_t e = cudaMallocAsync(&p, b < 256 ? 256 : b, s);
     if (e != cudaSuccess) {
         p = nullptr;

@@ -159,22 +159,93 @@ template <class Fn> __device__ __forceinline__ void for_arcs_vec(const SrcArgs &
     if (b1 + lane < j1) fn(b1 + lane, __ldg(a.col + b1 + lane));
 }
 
-// ------------------------------------------------------------------ top-down level d
-// Light frontier vertices: a warp takes 32 queue entries, stages (v, sigma[v], row
-// start, arcs before it) in shared memory and runs its lanes over the concatenated arcs;
-// the lane of arc i finds its vertex by binary search over the staged prefix sums.
-struct TdStage {
+// ------------------------------------------------------------------ lanes over arcs
+// A warp works on a group of up to 32 light vertices at a time: it stages their ids, row
+// starts and arc prefix sums in shared memory (with a per-vertex value: sigma for the
+// top-down push, a running sum for the pulls) and runs its 32 lanes over the concatenated
+// arcs, so that low-degree vertices leave no lane idle.  The lane of arc i finds its
+// vertex k by binary search over the staged prefix sums.
+struct LbStage {
     int v[32];
     int beg[32];
     int pre[33];
-    unsigned long long sv[32];
+    unsigned long long val[32];
 };
 
-__device__ void td_level(const SrcArgs &a, int d, int qo, int nf, int qnext, unsigned long long *s_mf,
-                         bool &ovf, TdStage *stages)
+// Stages the group (v = -1 or deg = 0 for no vertex) and returns its arc count.
+__device__ __forceinline__ int lb_stage(LbStage &st, int v, int deg, unsigned long long val, const int32_t *rp)
 {
     const int lane = threadIdx.x & 31;
-    TdStage &st = stages[threadIdx.x >> 5];
+    int incl = deg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    st.v[lane] = v;
+    st.beg[lane] = (v >= 0 && deg > 0) ? __ldg(rp + v) : 0;
+    st.pre[lane + 1] = incl;
+    st.val[lane] = val;
+    if (lane == 0) st.pre[0] = 0;
+    __syncwarp();
+    return __shfl_sync(FULL, incl, 31);
+}
+
+// The staged vertex of arc i of the group: the last k with pre[k] <= i.
+__device__ __forceinline__ int lb_find(const LbStage &st, int i)
+{
+    int lo = 0, hi = 31;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (st.pre[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Segmented sum over the lanes of one pass (lanes of the same vertex k are contiguous):
+// the first lane of each run of equal k receives the run's sum, which it adds to the
+// vertex's staged running sum.  x is a path count (uint64, carry out flagged) or a
+// double-single pair packed in 64 bits (PSI).
+template <bool PSI>
+__device__ __forceinline__ void lb_seg_add(LbStage &st, int k, bool valid, unsigned long long x, bool &ovf)
+{
+    const int lane = threadIdx.x & 31;
+    if (!valid) k = -1 - lane;  // a run of its own that adds nothing
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_down_sync(FULL, x, o);
+        const int k2 = __shfl_down_sync(FULL, k, o);
+        if (lane + o < 32 && k2 == k) {
+            if constexpr (PSI) {
+                x = dev::ff_pack(dev::ff_add(dev::ff_unpack(x), dev::ff_unpack(y)));
+            } else {
+                const unsigned long long z = x + y;
+                ovf |= z < x;
+                x = z;
+            }
+        }
+    }
+    const int kp = __shfl_up_sync(FULL, k, 1);
+    if (valid && (lane == 0 || kp != k)) {
+        if constexpr (PSI) {
+            st.val[k] = dev::ff_pack(dev::ff_add(dev::ff_unpack(st.val[k]), dev::ff_unpack(x)));
+        } else {
+            const unsigned long long z = st.val[k] + x;
+            ovf |= z < x;
+            st.val[k] = z;
+        }
+    }
+    __syncwarp();
+}
+
+// ------------------------------------------------------------------ top-down level d
+// Light frontier vertices: groups of 32 queue entries, lanes over their arcs.
+
+__device__ void td_level(const SrcArgs &a, int d, int qo, int nf, int qnext, unsigned long long *s_mf,
+                         bool &ovf, LbStage *stages)
+{
+    const int lane = threadIdx.x & 31;
+    LbStage &st = stages[threadIdx.x >> 5];
     const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long base = wid * 32; base < nf; base += nwarps * 32) {
@@ -184,27 +255,10 @@ __device__ void td_level(const SrcArgs &a, int d, int qo, int nf, int qnext, uns
             if ((unsigned)v < (unsigned)a.n && !heavy(a, v)) deg = degree(a.rp, v);
             else v = -1;
         }
-        int incl = deg;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += y;
-        }
-        st.v[lane] = v;
-        st.beg[lane] = v >= 0 ? __ldg(a.rp + v) : 0;
-        st.pre[lane + 1] = incl;
-        st.sv[lane] = v >= 0 ? __ldcg(a.sp + v) : 0ull;
-        if (lane == 0) st.pre[0] = 0;
-        __syncwarp();
-        const int total = __shfl_sync(FULL, incl, 31);
+        const int total = lb_stage(st, v, deg, v >= 0 ? __ldcg(a.sp + v) : 0ull, a.rp);
         for (int i = lane; i < total; i += 32) {
-            int lo = 0, hi = 31;  // last k with pre[k] <= i
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (st.pre[mid] <= i) lo = mid; else hi = mid - 1;
-            }
-            const int j = st.beg[lo] + (i - st.pre[lo]);
-            td_arc(a, d, __ldg(a.col + j), st.sv[lo], qnext, s_mf, ovf);
+            const int k = lb_find(st, i);
+            td_arc(a, d, __ldg(a.col + st.beg[k] + (i - st.pre[k])), st.val[k], qnext, s_mf, ovf);
         }
         __syncwarp();
     }
@@ -232,30 +286,35 @@ __device__ __forceinline__ void bu_settle(const SrcArgs &a, int d, int qnext, in
     atomicAdd(s_mf, (unsigned long long)degree(a.rp, w));
 }
 
-template <int TPV>
-__device__ void bu_level(const SrcArgs &a, int d, int qnext, unsigned long long *s_mf, bool &ovf)
+__device__ void bu_level(const SrcArgs &a, int d, int qnext, unsigned long long *s_mf, bool &ovf, LbStage *stages)
 {
-    constexpr int G = 32 / TPV;
-    const Lanes<TPV> L;
+    const int lane = threadIdx.x & 31;
+    LbStage &st = stages[threadIdx.x >> 5];
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const unsigned *cur = lvl_bits(a, d);
-    for (long long base = L.wid * G; base < a.n; base += L.nw * G) {
-        const long long w = base + L.gw;
-        const bool act = w < a.n && !test_bit(vis_bits(a), (int)w) && !heavy(a, (int)w);
-        unsigned long long acc = 0;
-        if (act) {
-            const int beg = __ldg(a.rp + w), end = __ldg(a.rp + w + 1);
-            for (int j = beg + L.lg; j < end; j += TPV) {
-                const int v = __ldg(a.col + j);
-                if (test_bit(cur, v)) {
-                    const unsigned long long y = acc + __ldcg(a.sp + v);
-                    ovf |= y < acc;
-                    acc = y;
-                }
+    // a warp takes the 32 vertices of one word of the visited bitmap
+    for (long long wd = wid; wd < a.nw; wd += nwarps) {
+        const unsigned visw = __ldcg(vis_bits(a) + wd);
+        if (visw == FULL) continue;  // warp-uniform
+        const long long w = wd * 32 + lane;
+        const bool act = w < a.n && !((visw >> lane) & 1u) && !heavy(a, (int)w);
+        const int total = lb_stage(st, act ? (int)w : -1, act ? degree(a.rp, (int)w) : 0, 0ull, a.rp);
+        for (int i0 = 0; i0 < total; i0 += 32) {
+            const int i = i0 + lane;
+            int k = 0;
+            unsigned long long x = 0;
+            if (i < total) {
+                k = lb_find(st, i);
+                const int v = __ldg(a.col + st.beg[k] + (i - st.pre[k]));
+                if (test_bit(cur, v)) x = __ldcg(a.sp + v);
             }
+            lb_seg_add<false>(st, k, i < total, x, ovf);
         }
-        acc = dev::group_sum_u64<TPV>(acc, ovf);
-        if (act && L.lg == 0 && acc != 0) bu_settle(a, d, qnext, (int)w, acc, s_mf);
+        if (act && st.val[lane] != 0) bu_settle(a, d, qnext, (int)w, st.val[lane], s_mf);
+        __syncwarp();
     }
+    const Lanes<32> L;
     // heavy unvisited vertices: per-chunk partial sums (finished by bu_heavy_finish)
     for (long long c = L.wid; c < a.C; c += L.nw) {
         int h, j0, j1;
@@ -305,37 +364,47 @@ __device__ __forceinline__ void finish_vertex(const SrcArgs &a, int v, dev::ff a
 
 // ------------------------------------------------------------------ backward level d
 // The level bitmap holds level d+1.
-template <int TPV>
-__device__ void back_level(const SrcArgs &a, int d, int qo, int nd)
+__device__ void back_level(const SrcArgs &a, int d, int qo, int nd, LbStage *stages)
 {
-    constexpr int G = 32 / TPV;
-    const Lanes<TPV> L;
+    const int lane = threadIdx.x & 31;
+    LbStage &st = stages[threadIdx.x >> 5];
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const unsigned *succ = lvl_bits(a, 0);
-    for (long long base = L.wid * G; base < nd; base += L.nw * G) {
-        const long long item = base + L.gw;
-        int v = -1;
-        if (item < nd) {
-            v = __ldcg(a.queue + qo + item);
-            if ((unsigned)v >= (unsigned)a.n || heavy(a, v)) v = -1;
+    for (long long base = wid * 32; base < nd; base += nwarps * 32) {
+        int v = -1, deg = 0;
+        if (base + lane < nd) {
+            v = __ldcg(a.queue + qo + base + lane);
+            if ((unsigned)v < (unsigned)a.n && !heavy(a, v)) deg = degree(a.rp, v);
+            else v = -1;
         }
-        dev::ff acc = dev::ff_zero();
-        if (v >= 0) {
-            // edge betweenness: the arc (v, w) carries sigma_v * psi_w = sigma_v / sigma_w *
-            // (1 + delta_w), read before v's own psi replaces sigma_v
-            const dev::ff sv = a.edge ? dev::ff_from_u64(__ldcg(a.sp + v)) : dev::ff_zero();
-            const int beg = __ldg(a.rp + v), end = __ldg(a.rp + v + 1);
-            for (int j = beg + L.lg; j < end; j += TPV) {
+        // edge betweenness: the arc (v, w) carries sigma_v * psi_w = sigma_v / sigma_w *
+        // (1 + delta_w), read before v's own psi replaces sigma_v; the staged value of
+        // vertex k is its running psi sum, and sigma_v is read per arc
+        const int total = lb_stage(st, v, deg, dev::ff_pack(dev::ff_zero()), a.rp);
+        for (int i0 = 0; i0 < total; i0 += 32) {
+            const int i = i0 + lane;
+            int k = 0;
+            unsigned long long x = dev::ff_pack(dev::ff_zero());
+            if (i < total) {
+                k = lb_find(st, i);
+                const int j = st.beg[k] + (i - st.pre[k]);
                 const int w = __ldg(a.col + j);
                 if (test_bit(succ, w)) {
-                    const dev::ff psi = dev::ff_unpack(__ldcg(a.sp + w));
-                    acc = dev::ff_add(acc, psi);
-                    if (a.edge) a.edge[j] += dev::ff_to_double(dev::ff_mul(sv, psi));
+                    x = __ldcg(a.sp + w);
+                    if (a.edge) {
+                        const dev::ff sv = dev::ff_from_u64(__ldcg(a.sp + st.v[k]));
+                        a.edge[j] += dev::ff_to_double(dev::ff_mul(sv, dev::ff_unpack(x)));
+                    }
                 }
             }
+            bool dummy = false;
+            lb_seg_add<true>(st, k, i < total, x, dummy);
         }
-        acc = dev::group_sum_ff<TPV>(acc);
-        if (v >= 0 && L.lg == 0) finish_vertex(a, v, acc, d);
+        if (v >= 0) finish_vertex(a, v, dev::ff_unpack(st.val[lane]), d);
+        __syncwarp();
     }
+    const Lanes<32> L;
     // heavy vertices of level d: per-chunk partial sums of psi
     for (long long c = L.wid; c < a.C; c += L.nw) {
         int h, j0, j1;
@@ -382,11 +451,10 @@ __device__ void mark_level(const SrcArgs &a, unsigned *b, int qo, int cnt, bool 
     }
 }
 
-template <int TPV>
-__global__ void __launch_bounds__(kThreads) k_source(SrcArgs a)
+__global__ void __launch_bounds__(kThreads, 3) k_source(SrcArgs a)
 {
     __shared__ unsigned long long s_mf;
-    __shared__ TdStage stages[kThreads / 32];
+    __shared__ LbStage stages[kThreads / 32];
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nthr = (long long)gridDim.x * blockDim.x;
     const int s = __ldg(a.src);
@@ -424,7 +492,7 @@ __global__ void __launch_bounds__(kThreads) k_source(SrcArgs a)
         const bool use_bu = a.dir == NK_DIR_BOTTOM_UP ||
                             (a.dir == NK_DIR_AUTO && a.alpha * (double)mf > (double)mu);
         if (use_bu) {
-            bu_level<TPV>(a, d, qnext, &s_mf, ovf);
+            bu_level(a, d, qnext, &s_mf, ovf, stages);
             if (a.H > 0) {
                 if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
                 bu_heavy_finish(a, d, qnext, &s_mf, ovf);
@@ -466,7 +534,7 @@ __global__ void __launch_bounds__(kThreads) k_source(SrcArgs a)
         if (l + 2 <= D) mark_level(a, lvl_bits(a, 0), __ldcg(a.qoff + l + 2), __ldcg(a.cnt + l + 2), false);
         if (l + 1 <= D) mark_level(a, lvl_bits(a, 0), __ldcg(a.qoff + l + 1), __ldcg(a.cnt + l + 1), true);
         if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
-        back_level<TPV>(a, l, ql, nl);
+        back_level(a, l, ql, nl, stages);
         if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
         if (a.H > 0) {
             back_heavy_finish(a, l);
@@ -539,42 +607,19 @@ struct Launch {
     int tpv;
 };
 
-template <int TPV> int make_launch(Launch &L)
+int make_launch(Launch &L)
 {
     static int blocks_per_sm = -1;
     if (blocks_per_sm < 0) {
         int b = 0;
-        NK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_source<TPV>, kThreads, 0));
+        NK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_source, kThreads, 0));
         blocks_per_sm = b;
     }
     if (blocks_per_sm < 1) return set_error(NK_ERR_CUDA, "per-source kernel cannot be resident");
-    L.fn = (const void *)k_source<TPV>;
+    L.fn = (const void *)k_source;
     L.grid = blocks_per_sm * num_sms();
-    L.tpv = TPV;
+    L.tpv = 32;  // lanes over arcs: a warp per group of up to 32 vertices
     return NK_OK;
-}
-
-int pick_launch(int tpv, Launch &L)
-{
-    switch (tpv) {
-    case 1: return make_launch<1>(L);
-    case 2: return make_launch<2>(L);
-    case 4: return make_launch<4>(L);
-    case 8: return make_launch<8>(L);
-    case 16: return make_launch<16>(L);
-    case 32: return make_launch<32>(L);
-    default: return set_error(NK_ERR_ARG, "threads per vertex must be 1, 2, 4, 8, 16 or 32 (got %d)", tpv);
-    }
-}
-
-int auto_tpv(const nk_graph *g)
-{
-    const double avg = g->n > 0 ? (double)g->A / g->n : 0.0;
-    if (avg <= 3) return 2;
-    if (avg <= 12) return 4;
-    if (avg <= 48) return 8;
-    if (avg <= 160) return 16;
-    return 32;
 }
 
 // workspace slots in nk_graph::ws used by this form
@@ -595,9 +640,8 @@ int run(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores, const Ru
     NK_TRY(ws[WS_CTRL].ensure(sizeof(Ctrl)));
     NK_TRY(build_heavy(g, s));
     NK_TRY(ws[WS_PART].ensure(sizeof(unsigned long long) * std::max<int64_t>(g->heavy_C, 1)));
-    const int tpv = cfg.tpv > 0 ? cfg.tpv : auto_tpv(g);
     Launch L;
-    NK_TRY(pick_launch(tpv, L));
+    NK_TRY(make_launch(L));
     SrcArgs a{};
     a.n = n;
     a.A = g->A;
@@ -672,7 +716,7 @@ int run(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores, const Ru
     if (st) {
         st->mode = NK_MODE_PER_SOURCE;
         st->batch = 1;
-        st->tpv = tpv;
+        st->tpv = L.tpv;
         st->max_depth = std::max(st->max_depth, h.depth);
         st->launches += k;
         st->td_levels += h.td_levels;
@@ -783,10 +827,8 @@ extern "C" int nk_sssp_noalloc(int32_t n, const int32_t *row_ptr, const int32_t 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     unsigned char *scr = nullptr;
     NK_TRY(noalloc_scratch(&scr));
-    const double avg = (double)n_arcs / n;
-    const int tpv = avg <= 3 ? 2 : avg <= 12 ? 4 : avg <= 48 ? 8 : avg <= 160 ? 16 : 32;
     Launch L;
-    NK_TRY(pick_launch(tpv, L));
+    NK_TRY(make_launch(L));
     SrcArgs a{};
     a.n = n;
     a.A = n_arcs;
