@@ -64,9 +64,9 @@ def test_committed_traffic_follows_kernel_sources():
     # the committed DRAM traffic is reported only while the kernel sources hash as captured
     # (after a kernel change it reads null until the capture is repeated)
     import bench
-    pj = json.load(open(os.path.join(ROOT, "profiles", "k_batch_rmat18_traffic.json")))
+    pj = json.load(open(os.path.join(ROOT, "profiles", "k_batch_rmat24_traffic.json")))
     current = pj["kernel_source_sha256"] == bench.kernel_source_hash(pj["kernel_sources"])
-    for key, batch, relabel in (("128", 128, False), ("128-relabelled", 128, True)):
-        want = pj["by_batch"][key]["dram_bytes_per_launch"] if current else None
-        assert bench.committed_traffic("rmat18", batch, relabel) == want
-    assert bench.committed_traffic("rmat18", 64) is None
+    want = pj["by_batch"]["128"]["dram_bytes_per_launch"] if current else None
+    assert bench.committed_traffic("rmat24", 128, False) == want
+    assert bench.committed_traffic("rmat24", 64) is None
+    assert bench.committed_traffic("rmat24", 128, True) is None
