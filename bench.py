@@ -661,6 +661,7 @@ def run_ours(args, world, rank, local):
     rp_h, col_h = g.export_csr()
     src_all = np.arange(n, dtype=np.int32) if exact else nk.sample_sources(n, sseed, k)
     k_arcs = sources_with_arcs(rp_h, src_all)
+    k_rank = len(nk.source_shard(src_all, rank, world)) if world > 1 else k
     k_rank_arcs = sources_with_arcs(rp_h, nk.source_shard(src_all, rank, world)) if world > 1 else k_arcs
     steps_launches = max(1, launches // max(args.steps, 1))
     alg = ((8.0 * A + 24.0 * n) * steps_launches + 34.0 * n * k_rank_arcs) / steps_launches
@@ -674,6 +675,12 @@ def run_ours(args, world, rank, local):
                 "algorithmic_bytes_per_launch": alg, "avg_launch_ms": per_launch_ms,
                 "launches_per_step": steps_launches,
                 "model": "per launch (8A + 24n) + 34n x (sources of the launch); sources without arcs are skipped"}
+    # the same byte model applied to every sampled source of the step (k of them, isolated ones
+    # included, as when every slot of a launch held a sampled source), over the step's kernel time
+    if not exact:
+        per_src = (8.0 * A + 24.0 * n) / B + 34.0 * n
+        roofline["achieved_per_sampled_source"] = per_src * (k_rank if world > 1 else k) / (kern_ms / max(args.steps, 1) / 1e3) / 1e9
+        roofline["frac_per_sampled_source"] = roofline["achieved_per_sampled_source"] / peak
     if traffic:
         # the DRAM bytes ncu counts per launch, over this run's average launch: the HBM rate the
         # kernel actually drives (its gathers re-read rows, so traffic exceeds the model)
@@ -704,7 +711,9 @@ def run_ours(args, world, rank, local):
     if not args.no_per_source and rank == 0 and not exact:
         P = min(args.per_source_sources, k)
         ps_src = torch.from_numpy(nk.sample_sources(n, sseed, k)[:P].copy()).cuda()
-        po = nk.run_opts(mode=nk.MODE_PER_SOURCE, flags=nk.RUN_TIME_KERNELS)
+        # the per-source form's own switch threshold (the batched form's tuned one does not
+        # carry over: alpha 4 is the fastest of 0.25..64 for single sources on R-MAT 24)
+        po = nk.run_opts(mode=nk.MODE_PER_SOURCE, alpha=4.0, flags=nk.RUN_TIME_KERNELS)
         nk.betweenness_sources(g, ps_src, 1.0, po, out=scores)
         torch.cuda.synchronize()
         pts, pk, pl = [], 0.0, 0
@@ -726,6 +735,7 @@ def run_ours(args, world, rank, local):
                              "tpv": ps["tpv"], "avg_launch_ms": plm,
                              "achieved_gbs": per_source_bytes(n, A) / (plm / 1e3) / 1e9,
                              "batched_speedup": (value / world) / ps_value,
+                             "alpha": 4.0,
                              "form": f"one persistent launch per source, the first {P} of the sampled set"}
 
     # ---- end to end through the C ABI with host buffers (pinned)
