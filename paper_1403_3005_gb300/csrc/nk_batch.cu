@@ -156,21 +156,34 @@ template <int W> __device__ __forceinline__ Bits<W> andnot(const Bits<W> &x, con
 
 __device__ __forceinline__ int deg_of(const int32_t *rp, int v) { return __ldg(rp + v + 1) - __ldg(rp + v); }
 
-// Source slots of a lane: lane L covers the adjacent source pairs {64q + 2L, 64q + 2L + 1}
-// of the batch's words q = 0..W-1, so that one 16-byte copy moves both of a pair's
-// values.  Slot k = 2q + e of lane L is source 64q + 2L + e: bit 2L + e of word q, and
-// entry 64q + 2L + e of a vertex's row of B values.
-__device__ __forceinline__ int slot_off(int k, int lane) { return 64 * (k >> 1) + 2 * lane + (k & 1); }
+// Source slots of a lane: lane L owns the G = 2W consecutive sources [G L, G L + G) of the
+// batch.  Slot k of lane L is source G L + k: bit G L + k of the batch's bitsets (word
+// (G L + k) / 64) and entry G L + k of a vertex's row of B values, so that one contiguous load
+// moves all of a lane's values of a row, and the lane's bits of a bitset are one field of one
+// word.
+template <int W> __device__ __forceinline__ int slot_off(int k, int lane) { return 2 * W * lane + k; }
+
+// The word of a bitset that holds the lane's slots (selected without indexing the register
+// array by a run-time value, which would move it to local memory).
+template <int W> __device__ __forceinline__ unsigned long long lane_word(const Bits<W> &b, int lane)
+{
+    unsigned long long w = b.w[0];
+#pragma unroll
+    for (int q = 1; q < W; ++q)
+        if (((2 * W * lane) >> 6) == q) w = b.w[q];
+    return w;
+}
 
 template <int W> __device__ __forceinline__ bool has_slot(const Bits<W> &b, int k, int lane)
 {
-    return (b.w[k >> 1] >> (2 * lane + (k & 1))) & 1ull;
+    return (lane_word<W>(b, lane) >> ((2 * W * lane + k) & 63)) & 1ull;
 }
 
-// The two bits of lane L's pair in word q.
-template <int W> __device__ __forceinline__ unsigned pair_bits(unsigned long long word, int lane)
+// The lane's 2W bits of a bitset of W words.
+template <int W> __device__ __forceinline__ unsigned lane_bits(const unsigned long long *w, int lane)
 {
-    return (unsigned)(word >> (2 * lane)) & 3u;
+    const int s = 2 * W * lane;
+    return (unsigned)(w[s >> 6] >> (s & 63)) & ((1u << (2 * W)) - 1u);
 }
 
 // bit i of x moved to bit 2i
@@ -182,6 +195,15 @@ __device__ __forceinline__ unsigned long long spread32(unsigned x)
     v = (v | (v << 4)) & 0x0F0F0F0F0F0F0F0Full;
     v = (v | (v << 2)) & 0x3333333333333333ull;
     v = (v | (v << 1)) & 0x5555555555555555ull;
+    return v;
+}
+
+// bit i of x (i < 64 / 2W) moved to bit 2W i
+template <int W> __device__ __forceinline__ unsigned long long spread_lanes(unsigned x)
+{
+    unsigned long long v = spread32(x);
+    if constexpr (W >= 2) v = spread32((unsigned)v);
+    if constexpr (W >= 4) v = spread32((unsigned)v);
     return v;
 }
 
@@ -269,35 +291,49 @@ __device__ __forceinline__ void gather(const BArgs &a, int beg, int end,
                 if (on[r]) left &= left - 1;
                 idx[r] = on[r] ? __popc(rel & ((1u << sr) - 1u)) : 0;
             }
-            ulonglong2 v[NB][W];
-            unsigned pb[NB][W];
+            // the lane's 2W bits of each listed neighbour, then one contiguous stretch of its row
+            // per neighbour: 2W entries of 4 bytes (32-bit sigma) or 8 bytes, in 16-byte loads,
+            // each issued only if one of its entries is relevant
+            constexpr int G = 2 * W;
+            unsigned nib[NB];
+            unsigned long long x[NB][G];
 #pragma unroll
             for (int r = 0; r < NB; ++r) {
-#pragma unroll
-                for (int q = 0; q < W; ++q) {
-                    pb[r][q] = on[r] ? pair_bits<W>(st.f[idx[r]][q], lane) : 0u;
-                    v[r][q] = make_ulonglong2(0ull, 0ull);
-                    if constexpr (S32) {
-                        // 32-bit sigma rows: one 8-byte load holds the lane's pair
-                        const unsigned *row = a.sp32 + (size_t)st.c[idx[r]] * B + 2 * lane;
-                        if (pb[r][q]) {
-                            const unsigned long long p = __ldcg(reinterpret_cast<const unsigned long long *>(row + 64 * q));
-                            v[r][q] = make_ulonglong2(p & 0xffffffffull, p >> 32);
-                        }
+                nib[r] = on[r] ? lane_bits<W>(st.f[idx[r]], lane) : 0u;
+                if constexpr (S32) {
+                    const unsigned *row = a.sp32 + (size_t)st.c[idx[r]] * B + G * lane;
+                    if constexpr (G == 2) {
+                        unsigned long long p = 0ull;
+                        if (nib[r]) p = __ldcg(reinterpret_cast<const unsigned long long *>(row));
+                        x[r][0] = p & 0xffffffffull;
+                        x[r][1] = p >> 32;
                     } else {
-                        const unsigned long long *row = a.sp + (size_t)st.c[idx[r]] * B + 2 * lane;
-                        if (pb[r][q]) v[r][q] = __ldcg(reinterpret_cast<const ulonglong2 *>(row + 64 * q));
+#pragma unroll
+                        for (int h = 0; h < G / 4; ++h) {
+                            uint4 p = make_uint4(0u, 0u, 0u, 0u);
+                            if ((nib[r] >> (4 * h)) & 15u) p = __ldcg(reinterpret_cast<const uint4 *>(row) + h);
+                            x[r][4 * h] = p.x;
+                            x[r][4 * h + 1] = p.y;
+                            x[r][4 * h + 2] = p.z;
+                            x[r][4 * h + 3] = p.w;
+                        }
+                    }
+                } else {
+                    const unsigned long long *row = a.sp + (size_t)st.c[idx[r]] * B + G * lane;
+#pragma unroll
+                    for (int h = 0; h < G / 2; ++h) {
+                        ulonglong2 p = make_ulonglong2(0ull, 0ull);
+                        if ((nib[r] >> (2 * h)) & 3u) p = __ldcg(reinterpret_cast<const ulonglong2 *>(row) + h);
+                        x[r][2 * h] = p.x;
+                        x[r][2 * h + 1] = p.y;
                     }
                 }
             }
-            unsigned long long x[NB][2 * W];
 #pragma unroll
             for (int r = 0; r < NB; ++r)
 #pragma unroll
-                for (int q = 0; q < W; ++q) {
-                    x[r][2 * q] = (pb[r][q] & 1u) ? v[r][q].x : 0ull;
-                    x[r][2 * q + 1] = (pb[r][q] & 2u) ? v[r][q].y : 0ull;
-                }
+                for (int k = 0; k < G; ++k)
+                    if (!((nib[r] >> k) & 1u)) x[r][k] = 0ull;
 #pragma unroll
             for (int k = 0; k < 2 * W; ++k) {
 #pragma unroll
@@ -342,12 +378,18 @@ __device__ __forceinline__ void gather(const BArgs &a, int beg, int end,
 
 template <int W> __device__ __forceinline__ Bits<W> nonzero_bits(const unsigned long long (&acc)[2 * W])
 {
+    // ballot k holds slot k of every lane; word q is lanes [32q/W, 32(q+1)/W), spread out
     Bits<W> r;
 #pragma unroll
-    for (int q = 0; q < W; ++q) {
-        const unsigned e0 = __ballot_sync(FULL, acc[2 * q] != 0ull);
-        const unsigned e1 = __ballot_sync(FULL, acc[2 * q + 1] != 0ull);
-        r.w[q] = spread32(e0) | (spread32(e1) << 1);
+    for (int q = 0; q < W; ++q) r.w[q] = 0ull;
+#pragma unroll
+    for (int k = 0; k < 2 * W; ++k) {
+        const unsigned m = __ballot_sync(FULL, acc[k] != 0ull);
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            const unsigned chunk = W == 1 ? m : (m >> (q * (32 / W))) & ((1u << (32 / W)) - 1u);
+            r.w[q] |= spread_lanes<W>(chunk) << k;
+        }
     }
     return r;
 }
@@ -374,7 +416,7 @@ __device__ __forceinline__ void settle(const BArgs &a, int w, const Bits<W> &vol
 #pragma unroll
         for (int k = 0; k < 2 * W; ++k)
             if (has_slot<W>(nb, k, lane)) {
-                row[slot_off(k, lane)] = (unsigned)acc[k];
+                row[slot_off<W>(k, lane)] = (unsigned)acc[k];
                 wide |= (acc[k] >> 32) != 0;
             }
         if (wide) atomicCAS(&a.ctrl->err, 0, kErrWide);
@@ -382,7 +424,7 @@ __device__ __forceinline__ void settle(const BArgs &a, int w, const Bits<W> &vol
         unsigned long long *row = a.sp + (size_t)w * B;
 #pragma unroll
         for (int k = 0; k < 2 * W; ++k)
-            if (has_slot<W>(nb, k, lane)) row[slot_off(k, lane)] = acc[k];
+            if (has_slot<W>(nb, k, lane)) row[slot_off<W>(k, lane)] = acc[k];
     }
     bool full = true;
 #pragma unroll
@@ -541,7 +583,7 @@ __device__ __forceinline__ void store_part(const BArgs &a, int c, const unsigned
 {
     unsigned long long *row = a.part + (size_t)c * (64 * W);
 #pragma unroll
-    for (int k = 0; k < 2 * W; ++k) row[slot_off(k, threadIdx.x & 31)] = acc[k];
+    for (int k = 0; k < 2 * W; ++k) row[slot_off<W>(k, threadIdx.x & 31)] = acc[k];
 }
 
 __device__ __forceinline__ bool heavy(const BArgs &a, int v) { return deg_of(a.rp, v) > a.chunk; }
@@ -697,7 +739,7 @@ __global__ void __launch_bounds__(kThreads, (W <= 2 ? 4 : 2)) k_batch(BArgs a)
                     const unsigned long long *row = a.part + (size_t)c * B;
 #pragma unroll
                     for (int k = 0; k < 2 * W; ++k) {
-                        const unsigned long long y = acc[k] + __ldcg(row + slot_off(k, lane));
+                        const unsigned long long y = acc[k] + __ldcg(row + slot_off<W>(k, lane));
                         ovf |= y < acc[k];
                         acc[k] = y;
                     }
@@ -777,7 +819,7 @@ __global__ void __launch_bounds__(kThreads, (W <= 2 ? 4 : 2)) k_batch(BArgs a)
                     const unsigned long long *row = a.part + (size_t)c * B;
 #pragma unroll
                     for (int k = 0; k < 2 * W; ++k) {
-                        const unsigned long long y = acc[k] + __ldcg(row + slot_off(k, lane));
+                        const unsigned long long y = acc[k] + __ldcg(row + slot_off<W>(k, lane));
                         ovf |= y < acc[k];
                         acc[k] = y;
                     }
@@ -914,11 +956,11 @@ __global__ void __launch_bounds__(kThreads, (W <= 2 ? 4 : 2)) k_batch(BArgs a)
 #pragma unroll
             for (int k = 0; k < 2 * W; ++k) {
                 if (has_slot<W>(mv, k, lane)) {
-                    const unsigned long long sg = S32 ? (unsigned long long)__ldcg(a.sp32 + (size_t)v * B + slot_off(k, lane))
-                                                      : __ldcg(row + slot_off(k, lane));
+                    const unsigned long long sg = S32 ? (unsigned long long)__ldcg(a.sp32 + (size_t)v * B + slot_off<W>(k, lane))
+                                                      : __ldcg(row + slot_off<W>(k, lane));
                     const dev::ff sv = dev::ff_from_u64(sg);
                     const dev::ff delta = dev::ff_mul(sv, facc[k]);
-                    row[slot_off(k, lane)] = dev::ff_pack(dev::ff_add(dev::ff_rcp(sv), facc[k]));
+                    row[slot_off<W>(k, lane)] = dev::ff_pack(dev::ff_add(dev::ff_rcp(sv), facc[k]));
                     part = dev::ff_add(part, delta);
                 }
             }
@@ -931,7 +973,7 @@ __global__ void __launch_bounds__(kThreads, (W <= 2 ? 4 : 2)) k_batch(BArgs a)
             const unsigned long long *row = a.sp + (size_t)v * B;
 #pragma unroll
             for (int k = 0; k < 2 * W; ++k)
-                sv[k] = has_slot<W>(mv, k, lane) ? dev::ff_from_u64(__ldcg(row + slot_off(k, lane))) : dev::ff_zero();
+                sv[k] = has_slot<W>(mv, k, lane) ? dev::ff_from_u64(__ldcg(row + slot_off<W>(k, lane))) : dev::ff_zero();
         };
         for_level<W>(a, ql, nl, Fl, a.wq + (size_t)l * 8 + WQ_BACK, [&](int v) {
             if (heavy(a, v)) return;
@@ -970,7 +1012,7 @@ __global__ void __launch_bounds__(kThreads, (W <= 2 ? 4 : 2)) k_batch(BArgs a)
             for (int c = c0; c < c1; ++c) {
                 const unsigned long long *row = a.part + (size_t)c * B;
 #pragma unroll
-                for (int k = 0; k < 2 * W; ++k) facc[k] = dev::ff_add(facc[k], dev::ff_unpack(__ldcg(row + slot_off(k, lane))));
+                for (int k = 0; k < 2 * W; ++k) facc[k] = dev::ff_add(facc[k], dev::ff_unpack(__ldcg(row + slot_off<W>(k, lane))));
             }
             finish(h, mv, facc);
         });

@@ -38,7 +38,10 @@
 
 #include <algorithm>
 #include <climits>
+#include <cstdio>
+#include <cstdlib>
 #include <mutex>
+#include <vector>
 
 #include "nk_device.cuh"
 #include "nk_internal.h"
@@ -76,7 +79,22 @@ struct SrcArgs {
     // bitmaps of nw = ceil(n / 32) words each: vis, then the two level bitmaps
     unsigned *bits;
     int32_t nw;
+    unsigned long long *trace;  // [kTraceCap][2] (code, globaltimer) after each barrier, or null
 };
+
+// Phase trace (diagnostics, NK_TRACE): CTA 0 records (level * 16 + phase, %globaltimer)
+// after a grid barrier.
+constexpr int kTraceCap = 512;
+enum { SPH_INIT = 1, SPH_TD, SPH_BU, SPH_BU_HUBS, SPH_POST, SPH_BK_MARK, SPH_BK, SPH_BK_HUBS };
+
+__device__ __forceinline__ void src_mark(const SrcArgs &a, int &ti, int level, int phase)
+{
+    if (a.trace && blockIdx.x == 0 && threadIdx.x == 0 && ti < kTraceCap) {
+        a.trace[2 * ti] = (unsigned long long)(level * 16 + phase);
+        a.trace[2 * ti + 1] = dev::globaltimer();
+        ++ti;
+    }
+}
 
 template <int TPV> struct Lanes {
     int lane, lg, gw;
@@ -459,6 +477,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_source(SrcArgs a)
     const long long nthr = (long long)gridDim.x * blockDim.x;
     const int s = __ldg(a.src);
     bool ovf = false;
+    int ti = 0;
+    src_mark(a, ti, 0, 0);
     for (long long v = tid; v < a.n; v += nthr) {
         a.dist[v] = v == s ? 0 : -1;
         a.sp[v] = v == s ? 1ull : 0ull;
@@ -477,6 +497,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_source(SrcArgs a)
         atomicOr(lvl_bits(a, 0) + (s >> 5), 1u << (s & 31));
     }
     if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+    src_mark(a, ti, 0, SPH_INIT);
     const int deg_s = degree(a.rp, s);
     long long mu = a.A - deg_s, mf = deg_s;
     int d = 0, qo = 0, nf = 1, td = 0, bu = 0;
@@ -495,6 +516,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_source(SrcArgs a)
             bu_level(a, d, qnext, &s_mf, ovf, stages);
             if (a.H > 0) {
                 if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+                src_mark(a, ti, d, SPH_BU);
                 bu_heavy_finish(a, d, qnext, &s_mf, ovf);
             }
         } else {
@@ -503,12 +525,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_source(SrcArgs a)
         __syncthreads();
         if (threadIdx.x == 0 && s_mf) atomicAdd((unsigned long long *)(a.mfa + d + 1), (unsigned long long)s_mf);
         if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+        src_mark(a, ti, d, use_bu ? (a.H > 0 ? SPH_BU_HUBS : SPH_BU) : SPH_TD);
         // level d+1 is complete: a top-down level adds it to vis (bottom-up set the bits as
         // it settled), and level d's bits leave its level bitmap for use by level d+2
         const int c = __ldcg(a.cnt + d + 1);
         if (!use_bu) mark_level(a, vis_bits(a), qnext, c, true);
         mark_level(a, lvl_bits(a, d), qo, nf, false);
         if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+        src_mark(a, ti, d, SPH_POST);
         const long long m2 = __ldcg(a.mfa + d + 1);
         if (use_bu) ++bu;
         else ++td;
@@ -534,11 +558,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_source(SrcArgs a)
         if (l + 2 <= D) mark_level(a, lvl_bits(a, 0), __ldcg(a.qoff + l + 2), __ldcg(a.cnt + l + 2), false);
         if (l + 1 <= D) mark_level(a, lvl_bits(a, 0), __ldcg(a.qoff + l + 1), __ldcg(a.cnt + l + 1), true);
         if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+        src_mark(a, ti, l, SPH_BK_MARK);
         back_level(a, l, ql, nl, stages);
         if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+        src_mark(a, ti, l, SPH_BK);
         if (a.H > 0) {
             back_heavy_finish(a, l);
             if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+            src_mark(a, ti, l, SPH_BK_HUBS);
         }
     }
 }
@@ -678,6 +705,13 @@ int run(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores, const Ru
         NK_CUDA(cudaEventRecord(e0, s));
     }
     if (cfg.far || cfg.rk_t) a.forward_only = 1;
+    static const bool trace_on = std::getenv("NK_TRACE") != nullptr;
+    Tmp trace_buf;
+    a.trace = nullptr;
+    if (trace_on) {
+        NK_TRY(trace_buf.alloc(sizeof(unsigned long long) * 2 * kTraceCap, s));
+        NK_CUDA(cudaMemsetAsync(trace_buf.p, 0, sizeof(unsigned long long) * 2 * kTraceCap, s));
+    }
     // sources without arcs add nothing to scores, arc shares or distance sums: only the
     // others are swept (not for a single-source sweep, whose outputs the caller reads, nor
     // for the error-bounded estimate, whose sources are tied to their targets)
@@ -695,6 +729,7 @@ int run(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores, const Ru
     }
     for (int32_t i = 0; i < k; ++i) {
         a.src = d_src + i;
+        a.trace = (trace_on && i == 0) ? trace_buf.as<unsigned long long>() : nullptr;
         void *args[] = {&a};
         int grid = std::max(1, L.grid / std::max(1, cfg.grid_div));
         if (cfg.grid_ctas > 0) grid = std::min(grid, cfg.grid_ctas);
@@ -713,6 +748,14 @@ int run(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores, const Ru
     Ctrl h;
     NK_CUDA(cudaMemcpyAsync(&h, a.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     NK_TRY(host_wait(s, k, a.limit_ns));
+    if (trace_on && k > 0) {
+        static const char *names[] = {"start", "init", "td", "bu", "bu+hubs", "post", "back-mark", "back", "back-hubs"};
+        std::vector<unsigned long long> t(2 * kTraceCap);
+        NK_CUDA(cudaMemcpy(t.data(), trace_buf.p, sizeof(unsigned long long) * t.size(), cudaMemcpyDeviceToHost));
+        for (int i = 1; i < kTraceCap && t[2 * i + 1]; ++i)
+            fprintf(stderr, "nk-trace per-source level=%llu phase=%s us=%.1f\n", t[2 * i] / 16,
+                    names[std::min<unsigned long long>(t[2 * i] % 16, 8)], (t[2 * i + 1] - t[2 * i - 1]) * 1e-3);
+    }
     if (st) {
         st->mode = NK_MODE_PER_SOURCE;
         st->batch = 1;
