@@ -422,12 +422,35 @@ def extension_legs(nk, torch, g, n, A, m, k, B, opts, stats, sseed, args, flush,
     base.flags |= nk.RUN_TIME_KERNELS
     reps = max(1, min(args.steps, 5))
 
+    def width(o, Bx):
+        oo = nk.RunOpts.from_buffer_copy(o)
+        oo.batch = Bx
+        return oo
+
+    def fastest(make_call):
+        """The faster of 128 and 256 sources per launch for one form (one untimed call of each
+        after a warm-up): the width the betweenness autotuner chose need not suit the forms
+        that differ from it (forward only, per-arc shares)."""
+        best = None
+        for Bx in (128, 256):
+            f = make_call(Bx)
+            f()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            f()
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
+            if best is None or t < best[1]:
+                best = (Bx, t)
+        return best[0]
+
     # closeness (Table 1): forward sweep and level sums
     far_d = torch.empty(n, dtype=torch.float64, device="cuda")
     reach_d = torch.empty(n, dtype=torch.float64, device="cuda")
-    ms, lms, st = timed(lambda: nk.closeness_sampled(g, sseed, k, base, out=(far_d, reach_d)), reps)
-    leg = {"value": m * k / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms, "batch": B,
-           "roofline": _roof(closeness_bytes(n, A, B, st["max_depth"] + 1), lms, peak, peak_kind, f"k_batch<W={B // 64}> forward only"),
+    Bc = fastest(lambda Bx: lambda: nk.closeness_sampled(g, sseed, k, width(base, Bx), out=(far_d, reach_d)))
+    ms, lms, st = timed(lambda: nk.closeness_sampled(g, sseed, k, width(base, Bc), out=(far_d, reach_d)), reps)
+    leg = {"value": m * k / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms, "batch": Bc,
+           "roofline": _roof(closeness_bytes(n, A, Bc, st["max_depth"] + 1), lms, peak, peak_kind, f"k_batch<W={Bc // 64}> forward only"),
            "form": "batched forward sweep, sampled sources, scale n/k"}
     if ora:
         o, rp_o, col_o, src_o = ora
@@ -444,9 +467,10 @@ def extension_legs(nk, torch, g, n, A, m, k, B, opts, stats, sseed, args, flush,
 
     # edge betweenness (Section 4.3)
     edge_d = torch.empty(A, dtype=torch.float64, device="cuda")
-    ms, lms, st = timed(lambda: nk.edge_betweenness_sampled(g, sseed, k, base, out=edge_d), reps)
-    leg = {"value": m * k / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms, "batch": B,
-           "roofline": _roof(edge_bytes(n, A, B), lms, peak, peak_kind, f"k_batch<W={B // 64}, EDGE>"),
+    Be = fastest(lambda Bx: lambda: nk.edge_betweenness_sampled(g, sseed, k, width(base, Bx), out=edge_d))
+    ms, lms, st = timed(lambda: nk.edge_betweenness_sampled(g, sseed, k, width(base, Be), out=edge_d), reps)
+    leg = {"value": m * k / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms, "batch": Be,
+           "roofline": _roof(edge_bytes(n, A, Be), lms, peak, peak_kind, f"k_batch<W={Be // 64}, EDGE>"),
            "form": "batched sweeps with per-arc shares, sampled sources, scale n/(2k)"}
     if ora:
         o, rp_o, col_o, src_o = ora
@@ -463,13 +487,15 @@ def extension_legs(nk, torch, g, n, A, m, k, B, opts, stats, sseed, args, flush,
 
     # error-bounded estimate (Section 3.2), epsilon 0.01, delta 0.1
     rk_eps, rk_delta = 0.01, 0.1
-    ro = nk.run_opts(mode=nk.MODE_BATCHED, batch=B, alpha=stats["alpha"], flags=nk.RUN_TIME_KERNELS)
     rk_out = torch.empty(n, dtype=torch.float64, device="cuda")
+    Br = fastest(lambda Bx: lambda: nk.betweenness_rk(g, rk_eps, rk_delta, sseed, nk.run_opts(
+        mode=nk.MODE_BATCHED, batch=Bx, alpha=stats["alpha"], flags=nk.RUN_TIME_KERNELS), out=rk_out))
+    ro = nk.run_opts(mode=nk.MODE_BATCHED, batch=Br, alpha=stats["alpha"], flags=nk.RUN_TIME_KERNELS)
     _, rk_r, rk_vd = nk.betweenness_rk(g, rk_eps, rk_delta, sseed, ro, out=rk_out)
     ms, lms, st = timed(lambda: nk.betweenness_rk(g, rk_eps, rk_delta, sseed, ro, out=rk_out), min(reps, 3))
     leg = {"value": m * rk_r / (ms / 1e3) / 1e9, "unit": UNIT, "ms_per_step": ms, "epsilon": rk_eps,
-           "delta": rk_delta, "samples": rk_r, "vertex_diameter_bound": rk_vd, "batch": B,
-           "roofline": _roof(rk_bytes(n, A, B), lms, peak, peak_kind, f"k_batch<W={B // 64}> forward + walks"),
+           "delta": rk_delta, "samples": rk_r, "vertex_diameter_bound": rk_vd, "batch": Br,
+           "roofline": _roof(rk_bytes(n, A, Br), lms, peak, peak_kind, f"k_batch<W={Br // 64}> forward + walks"),
            "form": "batched forward sweeps + one random path walk per sample"}
     if ora:
         o, rp_o, col_o, _ = ora

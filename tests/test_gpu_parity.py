@@ -635,3 +635,27 @@ def test_relabel_sampled_device_graph_and_autotune(nk):
     assert opts.flags & (nk.RUN_RELABEL | nk.RUN_NO_RELABEL)
     assert close(nk.betweenness_sampled(g, 5, 300, opts), want)
     assert close(nk.betweenness_sampled(g, 5, 300), want)   # the tuned choice, no options
+
+
+def test_sharded_helper_on_one_rank(nk):
+    # the GPU form of the split over ranks (sampler on the device, the rank's slice through
+    # nk_betweenness_sources, scale n/(2k)) in a one-rank NCCL group equals the plain call
+    import os
+    import socket
+    import torch
+    import torch.distributed as dist
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("nccl", rank=0, world_size=1)
+    try:
+        g = nk.graph_generate("rmat", 14, 5)
+        n = g.n
+        got = nk.betweenness_sampled_sharded(g, 9, 300, nk.run_opts(mode=nk.MODE_BATCHED, batch=64))
+        want = nk.betweenness_sampled(g, 9, 300, nk.run_opts(mode=nk.MODE_BATCHED, batch=64))
+        assert got.is_cuda and got.numel() == n
+        assert close(got.cpu().numpy(), want)
+        g.free()
+    finally:
+        dist.destroy_process_group()
