@@ -167,10 +167,11 @@ template <int W> __device__ __forceinline__ int slot_off(int k, int lane) { retu
 // array by a run-time value, which would move it to local memory).
 template <int W> __device__ __forceinline__ unsigned long long lane_word(const Bits<W> &b, int lane)
 {
-    unsigned long long w = b.w[0];
+    // mask-and-or over the words: a select chain can be turned into an indexed access
+    const int qi = (2 * W * lane) >> 6;
+    unsigned long long w = 0ull;
 #pragma unroll
-    for (int q = 1; q < W; ++q)
-        if (((2 * W * lane) >> 6) == q) w = b.w[q];
+    for (int q = 0; q < W; ++q) w |= b.w[q] & (0ull - (unsigned long long)(qi == q));
     return w;
 }
 
