@@ -187,27 +187,6 @@ template <int W> __device__ __forceinline__ unsigned lane_bits(const unsigned lo
     return (unsigned)(w[s >> 6] >> (s & 63)) & ((1u << (2 * W)) - 1u);
 }
 
-// bit i of x moved to bit 2i
-__device__ __forceinline__ unsigned long long spread32(unsigned x)
-{
-    unsigned long long v = x;
-    v = (v | (v << 16)) & 0x0000FFFF0000FFFFull;
-    v = (v | (v << 8)) & 0x00FF00FF00FF00FFull;
-    v = (v | (v << 4)) & 0x0F0F0F0F0F0F0F0Full;
-    v = (v | (v << 2)) & 0x3333333333333333ull;
-    v = (v | (v << 1)) & 0x5555555555555555ull;
-    return v;
-}
-
-// bit i of x (i < 64 / 2W) moved to bit 2W i
-template <int W> __device__ __forceinline__ unsigned long long spread_lanes(unsigned x)
-{
-    unsigned long long v = spread32(x);
-    if constexpr (W >= 2) v = spread32((unsigned)v);
-    if constexpr (W >= 4) v = spread32((unsigned)v);
-    return v;
-}
-
 // acc += x with the carry out of bit 63 counted in carry (a path-count overflow).
 __device__ __forceinline__ void add_carry(unsigned long long &acc, unsigned &carry, unsigned long long x)
 {
@@ -379,19 +358,19 @@ __device__ __forceinline__ void gather(const BArgs &a, int beg, int end,
 
 template <int W> __device__ __forceinline__ Bits<W> nonzero_bits(const unsigned long long (&acc)[2 * W])
 {
-    // ballot k holds slot k of every lane; word q is lanes [32q/W, 32(q+1)/W), spread out
+    // the lane's 2W-bit field, shifted into its place in its word, OR-reduced over the 32/W
+    // lanes that share the word, then every word broadcast from its first lane
+    constexpr int G = 2 * W, LPW = 32 / W;  // slots per lane, lanes per word
+    const int lane = threadIdx.x & 31;
+    unsigned f = 0u;
+#pragma unroll
+    for (int k = 0; k < G; ++k) f |= (acc[k] != 0ull ? 1u : 0u) << k;
+    unsigned long long v = (unsigned long long)f << ((G * lane) & 63);
+#pragma unroll
+    for (int o = 1; o < LPW; o <<= 1) v |= __shfl_xor_sync(FULL, v, o);
     Bits<W> r;
 #pragma unroll
-    for (int q = 0; q < W; ++q) r.w[q] = 0ull;
-#pragma unroll
-    for (int k = 0; k < 2 * W; ++k) {
-        const unsigned m = __ballot_sync(FULL, acc[k] != 0ull);
-#pragma unroll
-        for (int q = 0; q < W; ++q) {
-            const unsigned chunk = W == 1 ? m : (m >> (q * (32 / W))) & ((1u << (32 / W)) - 1u);
-            r.w[q] |= spread_lanes<W>(chunk) << k;
-        }
-    }
+    for (int q = 0; q < W; ++q) r.w[q] = __shfl_sync(FULL, v, q * LPW);
     return r;
 }
 
