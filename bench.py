@@ -860,6 +860,11 @@ def run_ours(args, world, rank, local):
                                  nk.last_run_stats(), sseed, args, flush, stream, ev0, ev1, side)
             for leg in ext.values():
                 leg["workload"] = side["workload"]
+            if "edge_betweenness" in ext:
+                # against vertex betweenness on the same graph and sources (tuned options, no
+                # CUDA graph: the edge call is not captured either)
+                vs = out["cuda_graph"]["same_call_without_graph"]["value"]
+                ext["edge_betweenness"]["fraction_of_vertex_sweep"] = ext["edge_betweenness"]["value"] / vs
             out.update(ext)
         if gs is not g:
             gs.free()

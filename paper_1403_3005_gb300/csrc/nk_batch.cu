@@ -209,7 +209,42 @@ template <int W> struct Nbrs {
     unsigned long long f[32][W];
     int c[32];
     int j[32];
+    double e[32];  // edge variant: each listed arc's share of the window
 };
+
+// sum_k sv[k] * x[k] over the lane's G slots (x: double-single pairs packed in 64 bits, zero
+// for slots that are not relevant), as a compensated dot product (Ogita, Rump and Oishi's
+// Dot2): the leading products hi*hi are summed by TwoSum, and their exact FMA errors, the
+// cross terms hi*lo and lo*hi and the TwoSum errors are gathered in one float instead of
+// renormalising the pair after every term.  All terms are non-negative (sigma and psi are),
+// so the gathered float stays a small fraction of the sum.
+template <int G>
+__device__ __forceinline__ dev::ff edge_dot(const dev::ff *sv, const unsigned long long (&x)[G])
+{
+    float s = 0.0f, c = 0.0f;
+#pragma unroll
+    for (int k = 0; k < G; ++k) {
+        const dev::ff b = dev::ff_unpack(x[k]);
+        const float p = __fmul_rn(sv[k].hi, b.hi);
+        c = __fmaf_rn(sv[k].hi, b.lo, __fmaf_rn(sv[k].lo, b.hi, __fadd_rn(c, __fmaf_rn(sv[k].hi, b.hi, -p))));
+        const float t = __fadd_rn(s, p);
+        const float z = __fsub_rn(t, s);
+        c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z)));  // TwoSum error
+        s = t;
+    }
+    return {s, c};  // not renormalised: edge_sum2 and ff_to_double take the pair as it is
+}
+
+// a + b for pairs whose second parts are small non-negative corrections (edge_dot's
+// results): the leading parts by TwoSum, its error and both corrections into the second
+// part, without renormalising
+__device__ __forceinline__ dev::ff edge_sum2(dev::ff a, dev::ff b)
+{
+    const float t = __fadd_rn(a.hi, b.hi);
+    const float z = __fsub_rn(t, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(t, z)), __fsub_rn(b.hi, z));
+    return {t, __fadd_rn(__fadd_rn(a.lo, b.lo), e)};
+}
 
 // For the warp's vertex with adjacency [beg, end): per source slot, the sum of sp over
 // the neighbours c whose Fsel[c] & tgt holds that source bit; uint64 sums (sigma, with
@@ -219,8 +254,10 @@ template <int W> struct Nbrs {
 // neighbours' loads in flight together) and add the relevant entries.
 // With EDGE (backward only) the warp's vertex v also hands every relevant arc (v, c) its
 // share sum_b sigma_b(v) * psi_b(c) over the gathered source bits (sv holds sigma_b(v) of
-// the lane's slots): a warp sum per neighbour, added to edge[j] by lane 0.  The arc is
-// owned by v's warp at this level, so no atomics are needed.
+// the lane's slots): a warp sum per neighbour, parked in shared memory, then added to
+// edge[j] by the lane that listed the arc, which loaded the old value when it listed it (the
+// load is in flight during the rounds, so no round waits on a read-modify-write).  The arc
+// is owned by v's warp at this level, so no atomics are needed.
 template <int W, bool PSI, bool EDGE = false, bool S32 = false>
 __device__ __forceinline__ void gather(const BArgs &a, int beg, int end,
                                        const unsigned long long *Fsel, const Bits<W> &tgt,
@@ -249,12 +286,14 @@ __device__ __forceinline__ void gather(const BArgs &a, int beg, int end,
         const bool mine = any_bits<W>(f);
         const unsigned rel = __ballot_sync(FULL, mine);
         if (!rel) continue;
+        const int pos = __popc(rel & dev::lanemask_lt());
+        double eold = 0.0;
         if (mine) {
-            const int pos = __popc(rel & dev::lanemask_lt());
             st.c[pos] = c;
             st.j[pos] = j;
 #pragma unroll
             for (int q = 0; q < W; ++q) st.f[pos][q] = f.w[q];
+            if constexpr (EDGE) eold = __ldcg(a.edge + j);
         }
         __syncwarp();
         // NB relevant neighbours per round (two for the edge variant): every load of the
@@ -326,12 +365,7 @@ __device__ __forceinline__ void gather(const BArgs &a, int beg, int end,
                 }
             }
             if constexpr (EDGE) {
-                dev::ff e0 = dev::ff_zero(), e1 = dev::ff_zero();
-#pragma unroll
-                for (int k = 0; k < 2 * W; ++k) {
-                    e0 = dev::ff_add(e0, dev::ff_mul(sv[k], dev::ff_unpack(x[0][k])));
-                    e1 = dev::ff_add(e1, dev::ff_mul(sv[k], dev::ff_unpack(x[NB - 1][k])));
-                }
+                const dev::ff e0 = edge_dot<G>(sv, x[0]), e1 = edge_dot<G>(sv, x[NB - 1]);
                 // both sums at once: one exchange leaves neighbour 0's partials in the low
                 // half-warp and neighbour 1's in the high half, then each half reduces alone
                 const bool lo = lane < 16;
@@ -339,19 +373,22 @@ __device__ __forceinline__ void gather(const BArgs &a, int beg, int end,
                 dev::ff recv;
                 recv.hi = __shfl_xor_sync(FULL, other.hi, 16);
                 recv.lo = __shfl_xor_sync(FULL, other.lo, 16);
-                mine = dev::ff_add(mine, recv);
+                mine = edge_sum2(mine, recv);
 #pragma unroll
                 for (int o = 8; o > 0; o >>= 1) {
                     dev::ff y;
                     y.hi = __shfl_xor_sync(FULL, mine.hi, o);
                     y.lo = __shfl_xor_sync(FULL, mine.lo, o);
-                    mine = dev::ff_add(mine, y);
+                    mine = edge_sum2(mine, y);
                 }
-                if (lane == 0) a.edge[st.j[idx[0]]] += dev::ff_to_double(mine);
-                if (on[NB - 1] && lane == 16) a.edge[st.j[idx[NB - 1]]] += dev::ff_to_double(mine);
+                if (lane == 0) st.e[idx[0]] = dev::ff_to_double(mine);
+                if (on[NB - 1] && lane == 16) st.e[idx[NB - 1]] = dev::ff_to_double(mine);
             }
         }
         __syncwarp();
+        if constexpr (EDGE) {
+            if (mine) a.edge[j] = eold + st.e[pos];
+        }
     }
     if (!PSI) ovf |= carry != 0;
 }
@@ -568,8 +605,13 @@ __device__ __forceinline__ void store_part(const BArgs &a, int c, const unsigned
 
 __device__ __forceinline__ bool heavy(const BArgs &a, int v) { return deg_of(a.rp, v) > a.chunk; }
 
+// CTAs per SM that the launch bounds ask for: 4 for 64 and 128 sources (64 registers), 3 for
+// the 128-source edge sweep (its per-arc shares need 80 registers, which 64 would spill), 2
+// for 256 sources
+template <int W, bool EDGE> constexpr int min_ctas() { return W >= 4 ? 2 : (EDGE && W == 2) ? 3 : 4; }
+
 template <int W, bool EDGE, bool S32>
-__global__ void __launch_bounds__(kThreads, (W <= 2 ? 4 : 2)) k_batch(BArgs a)
+__global__ void __launch_bounds__(kThreads, min_ctas<W, EDGE>()) k_batch(BArgs a)
 {
     constexpr int B = 64 * W;
     __shared__ BlockCnt bc;

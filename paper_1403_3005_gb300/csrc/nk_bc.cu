@@ -376,10 +376,25 @@ int closeness_entry(const nk_graph *gc, bool sample, uint64_t seed, int32_t k, d
     return NK_OK;
 }
 
-// Edge scores from per-arc sums: arc j = (u, v) gets scale * (arc[j] + arc[reverse of j]),
-// so both arcs of an edge hold the same value.  The row u of j and the reverse arc are
-// found by binary search (rows are sorted); a missing reverse arc sets *bad.
+// Position of v in the sorted row u of (rp, col), or -1.
+__device__ __forceinline__ int64_t find_arc(const int32_t *rp, const int32_t *col, int32_t u, int32_t v)
+{
+    int64_t b = __ldg(rp + u), e = __ldg(rp + u + 1);
+    const int64_t end = e;
+    while (b < e) {
+        const int64_t mid = b + (e - b) / 2;
+        if (__ldg(col + mid) < v) b = mid + 1; else e = mid;
+    }
+    return (b < end && __ldg(col + b) == v) ? b : -1;
+}
+
+// Edge scores from per-arc sums: arc j = (u, v) gets scale * (the sum of (u, v) + the sum of
+// (v, u)), so both arcs of an edge hold the same value.  The sums are indexed by the arcs of
+// the swept graph: the caller's graph (perm null) or its relabelled copy (rrp, rcol), whose
+// vertex perm[v] is the caller's v.  The row u of j is found by binary search over rp, the
+// swept arcs by binary search in their sorted rows; a missing arc sets *bad.
 __global__ void k_finish_edges(const int32_t *rp, const int32_t *col, int32_t n, int64_t A,
+                               const int32_t *perm, const int32_t *rrp, const int32_t *rcol,
                                const double *arc, double scale, double *out, int *bad)
 {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < A;
@@ -390,16 +405,19 @@ __global__ void k_finish_edges(const int32_t *rp, const int32_t *col, int32_t n,
             if ((int64_t)__ldg(rp + mid) <= j) lo = mid; else hi = mid;
         }
         const int32_t u = lo, v = __ldg(col + j);
-        int64_t b = __ldg(rp + v), e = __ldg(rp + v + 1);
-        while (b < e) {
-            const int64_t mid = b + (e - b) / 2;
-            if (__ldg(col + mid) < u) b = mid + 1; else e = mid;
+        int64_t j1 = j, j2;
+        if (perm) {
+            const int32_t pu = __ldg(perm + u), pv = __ldg(perm + v);
+            j1 = find_arc(rrp, rcol, pu, pv);
+            j2 = find_arc(rrp, rcol, pv, pu);
+        } else {
+            j2 = find_arc(rp, col, v, u);
         }
-        if (b >= __ldg(rp + v + 1) || __ldg(col + b) != u) {
+        if (j1 < 0 || j2 < 0) {
             atomicExch(bad, 1);
             continue;
         }
-        out[j] = scale * (arc[j] + arc[b]);
+        out[j] = scale * (arc[j1] + arc[j2]);
     }
 }
 
@@ -441,16 +459,29 @@ int edge_entry(const nk_graph *gc, bool sample, uint64_t seed, int32_t k, double
     cfg.edge = arc.as<double>();
     t_stats = RunStats();
     int mode = cfg.mode == NK_MODE_AUTO ? (k >= 16 ? NK_MODE_BATCHED : NK_MODE_PER_SOURCE) : cfg.mode;
+    // the batched sweep may run on the relabelled copy (as the vertex scores do): sources
+    // mapped in, the per-arc sums indexed by the copy's arcs and read back by k_finish_edges
+    const bool relab = cfg.relabel && mode == NK_MODE_BATCHED && build_relabeled(g, s) == NK_OK;
+    nk_graph *gs = relab ? g->relab.get() : g;
+    Tmp msrc;
+    const int32_t *sweep_src = dsrc.as<int32_t>();
+    if (relab) {
+        NK_TRY(msrc.alloc(sizeof(int32_t) * k, s));
+        k_map_ids<<<grid_of(k), 256, 0, s>>>(g->relab_perm.as<int32_t>(), dsrc.as<int32_t>(), k, msrc.as<int32_t>());
+        ::nk::count_launch();
+        sweep_src = msrc.as<int32_t>();
+        if (cfg.batch == 0 && g->tuned.valid) cfg.batch = g->tuned.batch;  // the copy is not tuned itself
+    }
     int rc;
     if (mode == NK_MODE_BATCHED) {
-        rc = run_batched(g, dsrc.as<int32_t>(), k, vsc.as<double>(), cfg, &t_stats, s);
+        rc = run_batched(gs, sweep_src, k, vsc.as<double>(), cfg, &t_stats, s);
         if (rc == NK_ERR_NOMEM && cfg.mode == NK_MODE_AUTO) {
             NK_TRY(zero());
             t_stats = RunStats();
-            rc = run_per_source(g, dsrc.as<int32_t>(), k, vsc.as<double>(), cfg, &t_stats, s);
+            rc = run_per_source(gs, sweep_src, k, vsc.as<double>(), cfg, &t_stats, s);
         }
     } else {
-        rc = run_per_source(g, dsrc.as<int32_t>(), k, vsc.as<double>(), cfg, &t_stats, s);
+        rc = run_per_source(gs, sweep_src, k, vsc.as<double>(), cfg, &t_stats, s);
     }
     NK_TRY(rc);
     double *dout = edge_scores;
@@ -462,7 +493,8 @@ int edge_entry(const nk_graph *gc, bool sample, uint64_t seed, int32_t k, double
     if (A > 0) {
         const int64_t blocks = std::min<int64_t>((A + 255) / 256, 16LL * num_sms());
         k_finish_edges<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, s>>>(
-            g->rp.as<int32_t>(), g->col.as<int32_t>(), n, A, arc.as<double>(), scale, dout, flag.as<int>());
+            g->rp.as<int32_t>(), g->col.as<int32_t>(), n, A, relab ? g->relab_perm.as<int32_t>() : nullptr,
+            gs->rp.as<int32_t>(), gs->col.as<int32_t>(), arc.as<double>(), scale, dout, flag.as<int>());
         ::nk::count_launch();
         NK_CUDA(cudaGetLastError());
     }

@@ -618,6 +618,29 @@ def test_relabel_parity(nk, name):
         assert close(got, want), (name, m)
 
 
+@pytest.mark.parametrize("name", ["hubs", "components", "grid", "star_big"])
+def test_relabel_edge_parity(nk, name):
+    # per-arc sums indexed by the copy's arcs, read back per caller arc (both directions)
+    g, rp, col = both(nk, SMALL[name])
+    n = len(rp) - 1
+    want = oracle.edge_betweenness_exact(rp, col)
+    for m in (dict(mode=2, batch=64), dict(mode=2, batch=128, direction=2), dict(mode=2, batch=256, chunk=64)):
+        got = nk.edge_betweenness_sampled(g, 3, n, nk.run_opts(flags=nk.RUN_RELABEL, **m))
+        assert close(got, want), (name, m)
+
+
+def test_relabel_edge_sampled_generated(nk):
+    import torch
+    g = nk.graph_generate("rmat", 13, 5)
+    n, rp, col = oracle.generate("rmat", 13, 5)
+    want = oracle.edge_betweenness_sampled(rp, col, 8, 300)
+    o = nk.run_opts(mode=2, batch=256, alpha=16.0, flags=nk.RUN_RELABEL)
+    assert close(nk.edge_betweenness_sampled(g, 8, 300, o), want)
+    out = torch.full((len(col),), -1.0, dtype=torch.float64, device="cuda")
+    nk.edge_betweenness_sampled(g, 8, 300, o, out=out)
+    assert close(out.cpu().numpy(), want)
+
+
 def test_relabel_sampled_device_graph_and_autotune(nk):
     import torch
     g = nk.graph_generate("rmat", 14, 3)
