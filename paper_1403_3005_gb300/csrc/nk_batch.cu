@@ -1201,7 +1201,6 @@ int launch_batches(nk_graph *g, const int32_t *d_src, int32_t k, double *d_score
         a.F = reinterpret_cast<unsigned long long *>(base + L.off_F);
         a.vis = reinterpret_cast<unsigned long long *>(base + L.off_vis);
         a.sp = reinterpret_cast<unsigned long long *>(base + L.off_sp);
-    a.sp32 = reinterpret_cast<unsigned *>(base + L.off_sp32);
         a.sp32 = reinterpret_cast<unsigned *>(base + L.off_sp32);
         a.qmark = reinterpret_cast<int32_t *>(base + L.off_qmark);
         a.queue = reinterpret_cast<int32_t *>(base + L.off_queue);

@@ -141,22 +141,33 @@ __device__ __forceinline__ void queue_append(const SrcArgs &a, int d, int qnext,
     if (qnext + pos < a.n) a.queue[qnext + pos] = w;
 }
 
-// Arc (v, w) of a top-down step from level d, sv = sigma[v]: w joins level d+1 unless an
-// earlier level holds it; the lane whose atomicOr sets w's bit in the level-(d+1) bitmap
-// claims and queues it; every such arc adds sigma[v] to sigma[w].
-__device__ __forceinline__ void td_arc(const SrcArgs &a, int d, int w, unsigned long long sv,
-                                       int qnext, unsigned long long *s_mf, bool &ovf)
+// Arcs (v_i, w[i]) of a top-down step from level d (w[i] < 0: none), sv[i] = sigma[v_i]: w
+// joins level d+1 unless an earlier level holds it; the lane whose atomicOr sets w's bit in
+// the level-(d+1) bitmap claims and queues it; every such arc adds sigma[v] to sigma[w].  The
+// N arcs go through each step together (N bit loads, then N claims, then N sigma adds, each
+// batch in flight at once) instead of one arc after the other.
+template <int N>
+__device__ __forceinline__ void td_arcs(const SrcArgs &a, int d, const int (&w)[N], const unsigned long long (&sv)[N],
+                                        int qnext, unsigned long long *s_mf, bool &ovf)
 {
-    if (test_bit(vis_bits(a), w)) return;
-    const unsigned bit = 1u << (w & 31);
-    const unsigned old = atomicOr(lvl_bits(a, d + 1) + (w >> 5), bit);
-    if (!(old & bit)) {
-        a.dist[w] = d + 1;
-        queue_append(a, d, qnext, w);
-        atomicAdd(s_mf, (unsigned long long)degree(a.rp, w));
+    bool go[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) go[i] = w[i] >= 0 && !test_bit(vis_bits(a), w[i]);
+    unsigned old[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) old[i] = go[i] ? atomicOr(lvl_bits(a, d + 1) + (w[i] >> 5), 1u << (w[i] & 31)) : 0u;
+    unsigned long long prev[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) prev[i] = go[i] ? atomicAdd(a.sp + w[i], sv[i]) : 0ull;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        if (go[i] && !((old[i] >> (w[i] & 31)) & 1u)) {
+            a.dist[w[i]] = d + 1;
+            queue_append(a, d, qnext, w[i]);
+            atomicAdd(s_mf, (unsigned long long)degree(a.rp, w[i]));
+        }
+        ovf |= go[i] && prev[i] + sv[i] < prev[i];
     }
-    const unsigned long long prev = atomicAdd(a.sp + w, sv);
-    ovf |= prev + sv < prev;
 }
 
 // fn(j, c) for every arc j of [j0, j1) with c = col[j], by the whole warp: a scalar head
@@ -175,6 +186,25 @@ template <class Fn> __device__ __forceinline__ void for_arcs_vec(const SrcArgs &
         fn(4 * q + 3, c4.w);
     }
     if (b1 + lane < j1) fn(b1 + lane, __ldg(a.col + b1 + lane));
+}
+
+// fn(j, c) for up to four arcs at a time by the whole warp (c[i] < 0: none): 16-byte column
+// loads of four arcs per lane, then the scalar head and tail (up to a 16-byte boundary)
+// together.
+template <class Fn> __device__ __forceinline__ void for_arcs_vec4(const SrcArgs &a, int j0, int j1, Fn fn)
+{
+    const int lane = threadIdx.x & 31;
+    const int b0 = min(j1, (j0 + 3) & ~3), b1 = max(b0, j1 & ~3);
+    for (int q = b0 / 4 + lane; q < b1 / 4; q += 32) {
+        const int4 c4 = __ldg(reinterpret_cast<const int4 *>(a.col) + q);
+        const int j[4] = {4 * q, 4 * q + 1, 4 * q + 2, 4 * q + 3};
+        const int c[4] = {c4.x, c4.y, c4.z, c4.w};
+        fn(j, c);
+    }
+    int j[4] = {j0 + lane, b1 + lane, 0, 0}, c[4] = {-1, -1, -1, -1};
+    if (j0 + lane < b0) c[0] = __ldg(a.col + j0 + lane);
+    if (b1 + lane < j1) c[1] = __ldg(a.col + b1 + lane);
+    if (__any_sync(FULL, c[0] >= 0 || c[1] >= 0)) fn(j, c);
 }
 
 // ------------------------------------------------------------------ lanes over arcs
@@ -274,9 +304,21 @@ __device__ void td_level(const SrcArgs &a, int d, int qo, int nf, int qnext, uns
             else v = -1;
         }
         const int total = lb_stage(st, v, deg, v >= 0 ? __ldcg(a.sp + v) : 0ull, a.rp);
-        for (int i = lane; i < total; i += 32) {
-            const int k = lb_find(st, i);
-            td_arc(a, d, __ldg(a.col + st.beg[k] + (i - st.pre[k])), st.val[k], qnext, s_mf, ovf);
+        for (int i0 = 0; i0 < total; i0 += 64) {  // two arcs per lane at a time
+            int w[2];
+            unsigned long long sv[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int i = i0 + 32 * u + lane;
+                w[u] = -1;
+                sv[u] = 0ull;
+                if (i < total) {
+                    const int k = lb_find(st, i);
+                    w[u] = __ldg(a.col + st.beg[k] + (i - st.pre[k]));
+                    sv[u] = st.val[k];
+                }
+            }
+            td_arcs<2>(a, d, w, sv, qnext, s_mf, ovf);
         }
         __syncwarp();
     }
@@ -285,8 +327,9 @@ __device__ void td_level(const SrcArgs &a, int d, int qo, int nf, int qnext, uns
         int h, j0, j1;
         chunk_of(a, c, h, j0, j1);
         if (__ldcg(a.dist + h) != d) continue;
-        const unsigned long long sv = __ldcg(a.sp + h);
-        for_arcs_vec(a, j0, j1, [&](int, int w) { td_arc(a, d, w, sv, qnext, s_mf, ovf); });
+        const unsigned long long s1 = __ldcg(a.sp + h);
+        const unsigned long long sv[4] = {s1, s1, s1, s1};
+        for_arcs_vec4(a, j0, j1, [&](const int (&)[4], const int (&w)[4]) { td_arcs<4>(a, d, w, sv, qnext, s_mf, ovf); });
     }
 }
 
@@ -318,16 +361,28 @@ __device__ void bu_level(const SrcArgs &a, int d, int qnext, unsigned long long 
         const long long w = wd * 32 + lane;
         const bool act = w < a.n && !((visw >> lane) & 1u) && !heavy(a, (int)w);
         const int total = lb_stage(st, act ? (int)w : -1, act ? degree(a.rp, (int)w) : 0, 0ull, a.rp);
-        for (int i0 = 0; i0 < total; i0 += 32) {
-            const int i = i0 + lane;
-            int k = 0;
-            unsigned long long x = 0;
-            if (i < total) {
-                k = lb_find(st, i);
-                const int v = __ldg(a.col + st.beg[k] + (i - st.pre[k]));
-                if (test_bit(cur, v)) x = __ldcg(a.sp + v);
+        for (int i0 = 0; i0 < total; i0 += 64) {
+            // two passes of 32 arcs at a time: both passes' column, bit and sigma loads are
+            // in flight before either reduction
+            int k[2], v[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int i = i0 + 32 * u + lane;
+                k[u] = 0;
+                v[u] = -1;
+                if (i < total) {
+                    k[u] = lb_find(st, i);
+                    v[u] = __ldg(a.col + st.beg[k[u]] + (i - st.pre[k[u]]));
+                }
             }
-            lb_seg_add<false>(st, k, i < total, x, ovf);
+            bool on[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) on[u] = v[u] >= 0 && test_bit(cur, v[u]);
+            unsigned long long x[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) x[u] = on[u] ? __ldcg(a.sp + v[u]) : 0ull;
+            lb_seg_add<false>(st, k[0], i0 + lane < total, x[0], ovf);
+            if (i0 + 32 < total) lb_seg_add<false>(st, k[1], i0 + 32 + lane < total, x[1], ovf);
         }
         if (act && st.val[lane] != 0) bu_settle(a, d, qnext, (int)w, st.val[lane], s_mf);
         __syncwarp();
@@ -400,24 +455,39 @@ __device__ void back_level(const SrcArgs &a, int d, int qo, int nd, LbStage *sta
         // (1 + delta_w), read before v's own psi replaces sigma_v; the staged value of
         // vertex k is its running psi sum, and sigma_v is read per arc
         const int total = lb_stage(st, v, deg, dev::ff_pack(dev::ff_zero()), a.rp);
-        for (int i0 = 0; i0 < total; i0 += 32) {
-            const int i = i0 + lane;
-            int k = 0;
-            unsigned long long x = dev::ff_pack(dev::ff_zero());
-            if (i < total) {
-                k = lb_find(st, i);
-                const int j = st.beg[k] + (i - st.pre[k]);
-                const int w = __ldg(a.col + j);
-                if (test_bit(succ, w)) {
-                    x = __ldcg(a.sp + w);
-                    if (a.edge) {
-                        const dev::ff sv = dev::ff_from_u64(__ldcg(a.sp + st.v[k]));
-                        a.edge[j] += dev::ff_to_double(dev::ff_mul(sv, dev::ff_unpack(x)));
-                    }
+        for (int i0 = 0; i0 < total; i0 += 64) {
+            // two passes of 32 arcs at a time: both passes' column, bit and psi loads are in
+            // flight before either reduction
+            int k[2], j[2], w[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int i = i0 + 32 * u + lane;
+                k[u] = 0;
+                j[u] = 0;
+                w[u] = -1;
+                if (i < total) {
+                    k[u] = lb_find(st, i);
+                    j[u] = st.beg[k[u]] + (i - st.pre[k[u]]);
+                    w[u] = __ldg(a.col + j[u]);
                 }
             }
+            bool on[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) on[u] = w[u] >= 0 && test_bit(succ, w[u]);
+            unsigned long long x[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) x[u] = on[u] ? __ldcg(a.sp + w[u]) : dev::ff_pack(dev::ff_zero());
+            if (a.edge) {
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+                    if (on[u]) {
+                        const dev::ff sv = dev::ff_from_u64(__ldcg(a.sp + st.v[k[u]]));
+                        a.edge[j[u]] += dev::ff_to_double(dev::ff_mul(sv, dev::ff_unpack(x[u])));
+                    }
+            }
             bool dummy = false;
-            lb_seg_add<true>(st, k, i < total, x, dummy);
+            lb_seg_add<true>(st, k[0], i0 + lane < total, x[0], dummy);
+            if (i0 + 32 < total) lb_seg_add<true>(st, k[1], i0 + 32 + lane < total, x[1], dummy);
         }
         if (v >= 0) finish_vertex(a, v, dev::ff_unpack(st.val[lane]), d);
         __syncwarp();
