@@ -72,6 +72,7 @@ struct SrcArgs {
     int dir;
     int forward_only;
     double *edge;        // [A] per-arc shares sigma_v * psi_w (edge betweenness), or null
+    double *acc;         // [n] psi sums pushed into light vertices (backward push levels)
     // rows longer than kHeavyChunk: chunk table and per-chunk partial sums
     const int32_t *hv, *hfirst, *chunk_h;
     int32_t H, C;
@@ -116,12 +117,41 @@ __device__ __forceinline__ int degree(const int32_t *rp, int v) { return __ldg(r
 __device__ __forceinline__ bool heavy(const SrcArgs &a, int v) { return a.H > 0 && degree(a.rp, v) > kHeavyChunk; }
 
 // Chunk c of a heavy vertex: its vertex h and arc range [j0, j1).
-__device__ __forceinline__ void chunk_of(const SrcArgs &a, long long c, int &h, int &j0, int &j1)
+// The arcs [j0, j1) of chunk c, whose heavy vertex is h.
+__device__ __forceinline__ void chunk_range(const SrcArgs &a, long long c, int h, int &j0, int &j1)
 {
-    const int i = __ldg(a.chunk_h + c);
-    h = __ldg(a.hv + i);
-    j0 = __ldg(a.rp + h) + (int)(c - __ldg(a.hfirst + i)) * kHeavyChunk;
+    j0 = __ldg(a.rp + h) + (int)(c - __ldg(a.hfirst + __ldg(a.chunk_h + c))) * kHeavyChunk;
     j1 = min(j0 + kHeavyChunk, __ldg(a.rp + h + 1));
+}
+
+// fn(c, h, j0, j1) by the whole warp for every chunk c whose heavy vertex h passes keep(h).
+// Warp w takes the chunks w + i * nwarps, so that the consecutive chunks of one hub go to
+// different warps.  Its lanes test the owners of 32 of them at once and the warp then walks
+// the chunks that passed: a level with few hubs on it costs a few ballots per warp instead
+// of a chain of dependent loads for every chunk of the graph.
+template <class Keep, class Fn> __device__ __forceinline__ void for_chunks(const SrcArgs &a, Keep keep, Fn fn)
+{
+    const int lane = threadIdx.x & 31;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long i0 = 0; wid + i0 * nwarps < a.C; i0 += 32) {
+        const long long cl = wid + (i0 + lane) * nwarps;
+        int h = -1;
+        if (cl < a.C) {
+            h = __ldg(a.hv + __ldg(a.chunk_h + cl));
+            if (!keep(h)) h = -1;
+        }
+        unsigned m = __ballot_sync(FULL, h >= 0);
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            const long long c = wid + (i0 + b) * nwarps;
+            const int hb = __shfl_sync(FULL, h, b);
+            int j0, j1;
+            chunk_range(a, c, hb, j0, j1);
+            fn(c, hb, j0, j1);
+        }
+    }
 }
 
 // bitmaps: vis = bits[0, nw), level bitmap p = bits[(1 + p) nw, (2 + p) nw)
@@ -323,14 +353,11 @@ __device__ void td_level(const SrcArgs &a, int d, int qo, int nf, int qnext, uns
         __syncwarp();
     }
     // heavy frontier vertices: one warp per chunk of kHeavyChunk arcs
-    for (long long c = wid; c < a.C; c += nwarps) {
-        int h, j0, j1;
-        chunk_of(a, c, h, j0, j1);
-        if (__ldcg(a.dist + h) != d) continue;
+    for_chunks(a, [&](int h) { return __ldcg(a.dist + h) == d; }, [&](long long, int h, int j0, int j1) {
         const unsigned long long s1 = __ldcg(a.sp + h);
         const unsigned long long sv[4] = {s1, s1, s1, s1};
         for_arcs_vec4(a, j0, j1, [&](const int (&)[4], const int (&w)[4]) { td_arcs<4>(a, d, w, sv, qnext, s_mf, ovf); });
-    }
+    });
 }
 
 // ------------------------------------------------------------------ bottom-up level d
@@ -354,10 +381,18 @@ __device__ void bu_level(const SrcArgs &a, int d, int qnext, unsigned long long 
     const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const unsigned *cur = lvl_bits(a, d);
-    // a warp takes the 32 vertices of one word of the visited bitmap
-    for (long long wd = wid; wd < a.nw; wd += nwarps) {
-        const unsigned visw = __ldcg(vis_bits(a) + wd);
-        if (visw == FULL) continue;  // warp-uniform
+    // a warp takes the 32 vertices of one word of the visited bitmap: its words are
+    // wid + i * nwarps, read 32 at a time (a lane each), and the words with an unvisited
+    // vertex are walked in turn
+    for (long long i0 = 0; wid + i0 * nwarps < a.nw; i0 += 32) {
+        const long long wl = wid + (i0 + lane) * nwarps;
+        const unsigned vl = wl < a.nw ? __ldcg(vis_bits(a) + wl) : FULL;
+        unsigned open = __ballot_sync(FULL, vl != FULL);
+      while (open) {
+        const int b = __ffs(open) - 1;
+        open &= open - 1;
+        const long long wd = wid + (i0 + b) * nwarps;
+        const unsigned visw = __shfl_sync(FULL, vl, b);
         const long long w = wd * 32 + lane;
         const bool act = w < a.n && !((visw >> lane) & 1u) && !heavy(a, (int)w);
         const int total = lb_stage(st, act ? (int)w : -1, act ? degree(a.rp, (int)w) : 0, 0ull, a.rp);
@@ -386,13 +421,10 @@ __device__ void bu_level(const SrcArgs &a, int d, int qnext, unsigned long long 
         }
         if (act && st.val[lane] != 0) bu_settle(a, d, qnext, (int)w, st.val[lane], s_mf);
         __syncwarp();
+      }
     }
-    const Lanes<32> L;
     // heavy unvisited vertices: per-chunk partial sums (finished by bu_heavy_finish)
-    for (long long c = L.wid; c < a.C; c += L.nw) {
-        int h, j0, j1;
-        chunk_of(a, c, h, j0, j1);
-        if (test_bit(vis_bits(a), h)) continue;
+    for_chunks(a, [&](int h) { return !test_bit(vis_bits(a), h); }, [&](long long c, int, int j0, int j1) {
         unsigned long long acc = 0;
         for_arcs_vec(a, j0, j1, [&](int, int v) {
             if (test_bit(cur, v)) {
@@ -402,8 +434,8 @@ __device__ void bu_level(const SrcArgs &a, int d, int qnext, unsigned long long 
             }
         });
         acc = dev::group_sum_u64<32>(acc, ovf);
-        if (L.lane == 0) a.part[c] = acc;
-    }
+        if (lane == 0) a.part[c] = acc;
+    });
 }
 
 // After a barrier: heavy unvisited vertices add their chunk sums in chunk order.
@@ -437,14 +469,14 @@ __device__ __forceinline__ void finish_vertex(const SrcArgs &a, int v, dev::ff a
 
 // ------------------------------------------------------------------ backward level d
 // The level bitmap holds level d+1.
-__device__ void back_level(const SrcArgs &a, int d, int qo, int nd, LbStage *stages)
+__device__ void back_level(const SrcArgs &a, int d, int qo, int nd, LbStage *stages, bool light = true)
 {
     const int lane = threadIdx.x & 31;
     LbStage &st = stages[threadIdx.x >> 5];
     const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const unsigned *succ = lvl_bits(a, 0);
-    for (long long base = wid * 32; base < nd; base += nwarps * 32) {
+    for (long long base = wid * 32; light && base < nd; base += nwarps * 32) {
         int v = -1, deg = 0;
         if (base + lane < nd) {
             v = __ldcg(a.queue + qo + base + lane);
@@ -492,12 +524,8 @@ __device__ void back_level(const SrcArgs &a, int d, int qo, int nd, LbStage *sta
         if (v >= 0) finish_vertex(a, v, dev::ff_unpack(st.val[lane]), d);
         __syncwarp();
     }
-    const Lanes<32> L;
     // heavy vertices of level d: per-chunk partial sums of psi
-    for (long long c = L.wid; c < a.C; c += L.nw) {
-        int h, j0, j1;
-        chunk_of(a, c, h, j0, j1);
-        if (__ldcg(a.dist + h) != d) continue;
+    for_chunks(a, [&](int h) { return __ldcg(a.dist + h) == d; }, [&](long long c, int h, int j0, int j1) {
         dev::ff acc = dev::ff_zero();
         const dev::ff sv = a.edge ? dev::ff_from_u64(__ldcg(a.sp + h)) : dev::ff_zero();
         for_arcs_vec(a, j0, j1, [&](int j, int w) {
@@ -508,7 +536,107 @@ __device__ void back_level(const SrcArgs &a, int d, int qo, int nd, LbStage *sta
             }
         });
         acc = dev::group_sum_ff<32>(acc);
-        if (L.lane == 0) a.part[c] = dev::ff_pack(acc);
+        if (lane == 0) a.part[c] = dev::ff_pack(acc);
+    });
+}
+
+// ------------------------------------------------------------------ backward push, level d
+// A level whose successors (level d+1) carry far fewer arcs than itself takes their psi by
+// push instead of pull: every arc (w, v) of a level-(d+1) vertex w whose end v is a light
+// vertex of level d (bit in level bitmap 1) adds psi_w to acc[v] with an FP64 atomic; heavy
+// vertices of level d still pull over their chunks, so no hub takes a stream of atomics.
+// Edge betweenness: the arc (w, v) carries sigma_v * psi_w (its reverse arc is summed in by
+// the finishing pass over arcs).  The level bitmap 0 holds level d+1.
+
+// Marks the light vertices of level d in level bitmap 1 and zeroes their sums.
+__device__ void mark_push_targets(const SrcArgs &a, int qo, int cnt)
+{
+    unsigned *b = lvl_bits(a, 1);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int v = __ldcg(a.queue + qo + i);
+        if ((unsigned)v >= (unsigned)a.n || heavy(a, v)) continue;
+        atomicOr(b + (v >> 5), 1u << (v & 31));
+        a.acc[v] = 0.0;
+    }
+}
+
+// Arc (w, v), j its index, pk = psi_w (packed double-single): adds psi_w to v's sum if v is
+// a push target (on).
+__device__ __forceinline__ void push_arc(const SrcArgs &a, int j, int v, unsigned long long pk, bool on)
+{
+    if (!on) return;
+    const dev::ff pw = dev::ff_unpack(pk);
+    atomicAdd(a.acc + v, dev::ff_to_double(pw));
+    if (a.edge) a.edge[j] += dev::ff_to_double(dev::ff_mul(dev::ff_from_u64(__ldcg(a.sp + v)), pw));
+}
+
+__device__ void back_push(const SrcArgs &a, int d, int qo1, int n1, LbStage *stages)
+{
+    const int lane = threadIdx.x & 31;
+    LbStage &st = stages[threadIdx.x >> 5];
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const unsigned *tgt = lvl_bits(a, 1);
+    // light vertices of level d+1: groups of 32 queue entries, lanes over their arcs
+    for (long long base = wid * 32; base < n1; base += nwarps * 32) {
+        int w = -1, deg = 0;
+        if (base + lane < n1) {
+            w = __ldcg(a.queue + qo1 + base + lane);
+            if ((unsigned)w < (unsigned)a.n && !heavy(a, w)) deg = degree(a.rp, w);
+            else w = -1;
+        }
+        const int total = lb_stage(st, w, deg, w >= 0 ? __ldcg(a.sp + w) : 0ull, a.rp);
+        for (int i0 = 0; i0 < total; i0 += 64) {  // two arcs per lane at a time
+            int j[2], v[2];
+            unsigned long long pk[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int i = i0 + 32 * u + lane;
+                j[u] = 0;
+                v[u] = -1;
+                pk[u] = 0ull;
+                if (i < total) {
+                    const int k = lb_find(st, i);
+                    j[u] = st.beg[k] + (i - st.pre[k]);
+                    v[u] = __ldg(a.col + j[u]);
+                    pk[u] = st.val[k];
+                }
+            }
+            bool on[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) on[u] = v[u] >= 0 && test_bit(tgt, v[u]);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) push_arc(a, j[u], v[u], pk[u], on[u]);
+        }
+        __syncwarp();
+    }
+    // heavy vertices of level d+1: one warp per chunk
+    for_chunks(a, [&](int h) { return __ldcg(a.dist + h) == d + 1; }, [&](long long, int h, int j0, int j1) {
+        const unsigned long long pk = __ldcg(a.sp + h);
+        for_arcs_vec4(a, j0, j1, [&](const int (&j)[4], const int (&v)[4]) {
+            bool on[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) on[u] = v[u] >= 0 && test_bit(tgt, v[u]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) push_arc(a, j[u], v[u], pk, on[u]);
+        });
+    });
+}
+
+// After a barrier: the light vertices of level d finish with their pushed sums (and leave
+// level bitmap 1); the heavy ones add their chunk sums.
+__device__ void back_push_finish(const SrcArgs &a, int d, int qo, int cnt)
+{
+    unsigned *b = lvl_bits(a, 1);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int v = __ldcg(a.queue + qo + i);
+        if ((unsigned)v >= (unsigned)a.n || heavy(a, v)) continue;
+        const double x = __ldcg(a.acc + v);
+        const float hi = __double2float_rn(x);
+        finish_vertex(a, v, {hi, __double2float_rn(x - (double)hi)}, d);
+        atomicAnd(b + (v >> 5), ~(1u << (v & 31)));
     }
 }
 
@@ -549,11 +677,21 @@ __global__ void __launch_bounds__(kThreads, 3) k_source(SrcArgs a)
     bool ovf = false;
     int ti = 0;
     src_mark(a, ti, 0, 0);
-    for (long long v = tid; v < a.n; v += nthr) {
-        a.dist[v] = v == s ? 0 : -1;
-        a.sp[v] = v == s ? 1ull : 0ull;
+    // vertices without arcs start out visited (their distance stays -1): no arc reaches
+    // them, and the bottom-up levels then skip the words in which every vertex with arcs
+    // has been reached; a warp covers 32 consecutive vertices, one word of the bitmap
+    for (long long v0 = tid - (tid & 31); v0 < a.n; v0 += nthr) {
+        const long long v = v0 + (threadIdx.x & 31);
+        bool iso = false;
+        if (v < a.n) {
+            a.dist[v] = v == s ? 0 : -1;
+            a.sp[v] = v == s ? 1ull : 0ull;
+            iso = degree(a.rp, (int)v) == 0;
+        }
+        const unsigned w = __ballot_sync(FULL, iso);
+        if ((threadIdx.x & 31) == 0) vis_bits(a)[v0 >> 5] = w;
     }
-    for (long long i = tid; i < 3LL * a.nw; i += nthr) a.bits[i] = 0u;
+    for (long long i = tid; i < 2LL * a.nw; i += nthr) a.bits[a.nw + i] = 0u;
     if (tid == 0) {
         a.queue[0] = s;
         a.cnt[0] = 1;
@@ -625,10 +763,28 @@ __global__ void __launch_bounds__(kThreads, 3) k_source(SrcArgs a)
     // swept (edge betweenness also sweeps level 0: the source's arcs carry shares)
     for (int l = D; l >= (a.edge ? 0 : 1); --l) {
         const int ql = __ldcg(a.qoff + l), nl = __ldcg(a.cnt + l);
+        // push when the successors' arcs are under a quarter of this level's and the level's
+        // vertices average more than 16 arcs (marking and finishing cost a pass over the
+        // level's vertices, which a level of few arcs per vertex does not repay); the arc
+        // sums and counts per level come from the forward sweep and read the same in every CTA
+        const long long arcs_l = __ldcg(a.mfa + l);
+        const bool push = l >= 1 && l + 1 <= D && 4LL * __ldcg(a.mfa + l + 1) < arcs_l && arcs_l > 16LL * nl;
         if (l + 2 <= D) mark_level(a, lvl_bits(a, 0), __ldcg(a.qoff + l + 2), __ldcg(a.cnt + l + 2), false);
         if (l + 1 <= D) mark_level(a, lvl_bits(a, 0), __ldcg(a.qoff + l + 1), __ldcg(a.cnt + l + 1), true);
+        if (push) mark_push_targets(a, ql, nl);
         if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
         src_mark(a, ti, l, SPH_BK_MARK);
+        if (push) {
+            back_push(a, l, __ldcg(a.qoff + l + 1), __ldcg(a.cnt + l + 1), stages);
+            back_level(a, l, ql, nl, stages, false);  // heavy vertices of level l pull
+            if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+            src_mark(a, ti, l, SPH_BK);
+            back_push_finish(a, l, ql, nl);
+            if (a.H > 0) back_heavy_finish(a, l);
+            if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
+            src_mark(a, ti, l, SPH_BK_HUBS);
+            continue;
+        }
         back_level(a, l, ql, nl, stages);
         if (!dev::grid_barrier(a.ctrl, a.limit_ns)) return;
         src_mark(a, ti, l, SPH_BK);
@@ -729,7 +885,9 @@ int run(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores, const Ru
     const int32_t n = g->n;
     DevBuf *ws = scratch(cfg, g);
     NK_TRY(ws[WS_DIST].ensure(sizeof(int32_t) * n));
-    NK_TRY(ws[WS_SP].ensure(sizeof(uint64_t) * n));
+    // sp, then (for a backward sweep) the FP64 sums of the push levels
+    const bool fwd_only = forward_only || cfg.far || cfg.rk_t;
+    NK_TRY(ws[WS_SP].ensure(sizeof(uint64_t) * (size_t)n * (fwd_only ? 1 : 2)));
     NK_TRY(ws[WS_QUEUE].ensure(sizeof(int32_t) * n));
     const size_t lv = (size_t)n + 3;
     const int32_t nw = (n + 31) / 32;
@@ -761,6 +919,7 @@ int run(nk_graph *g, const int32_t *d_src, int32_t k, double *d_scores, const Ru
     a.dir = cfg.direction;
     a.forward_only = forward_only ? 1 : 0;
     a.edge = forward_only ? nullptr : cfg.edge;
+    a.acc = fwd_only ? nullptr : reinterpret_cast<double *>(ws[WS_SP].as<unsigned long long>() + n);
     a.hv = g->heavy[0].as<int32_t>();
     a.hfirst = g->heavy[1].as<int32_t>();
     a.chunk_h = g->heavy[2].as<int32_t>();

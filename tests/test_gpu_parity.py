@@ -246,6 +246,33 @@ def test_sampled_rmat_modes(nk, m):
     assert close(got, want), m
 
 
+def test_per_source_push_levels(nk):
+    # sources whose sweep has a level l >= 1 with 4 * arcs(l + 1) < arcs(l) and a hub (more
+    # than 256 arcs) on it: the per-source backward pushes psi into that level's light
+    # vertices and pulls for its hubs
+    g = nk.graph_generate("rmat", 14, 3)
+    n, rp, col = oracle.generate("rmat", 14, 3)
+    deg = np.diff(rp)
+    picked = []
+    for s in oracle.sample_sources(n, 6, 400):
+        if deg[s] == 0:
+            continue
+        d, _ = oracle.bfs(rp, col, int(s))
+        arcs = np.bincount(d[d >= 0], weights=deg[d >= 0])
+        hubs = np.bincount(d[(d >= 0) & (deg > 256)], minlength=len(arcs))
+        if any(4 * arcs[l + 1] < arcs[l] and hubs[l] > 0 for l in range(1, len(arcs) - 1)):
+            picked.append(int(s))
+        if len(picked) == 24:
+            break
+    assert len(picked) == 24
+    src = np.array(picked, dtype=np.int32)
+    want = oracle.betweenness_sources(rp, col, src, 0.5)
+    assert close(nk.betweenness_sources(g, src, 0.5, nk.run_opts(mode=1)), want)
+    assert close(nk.betweenness_sources(g, src, 0.5, nk.run_opts(mode=1, direction=1)), want)
+    want_e = oracle.edge_betweenness_sampled(rp, col, 6, 400)   # the whole sample they come from
+    assert close(nk.edge_betweenness_sampled(g, 6, 400, nk.run_opts(mode=1)), want_e)
+
+
 def test_sampled_ba_and_isolated_sources(nk):
     # R-MAT leaves many isolated vertices: sampled sources that are isolated count
     g = nk.graph_generate("rmat", 11, 9, edge_factor=2)
