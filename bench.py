@@ -428,18 +428,20 @@ def extension_legs(nk, torch, g, n, A, m, k, B, opts, stats, sseed, args, flush,
         return oo
 
     def fastest(make_call):
-        """The faster of 128 and 256 sources per launch for one form (one untimed call of each
-        after a warm-up): the width the betweenness autotuner chose need not suit the forms
-        that differ from it (forward only, per-arc shares)."""
+        """The faster of 128 and 256 sources per launch for one form (the best of three calls
+        of each after a warm-up): the width the betweenness autotuner chose need not suit the
+        forms that differ from it (forward only, per-arc shares)."""
         best = None
         for Bx in (128, 256):
             f = make_call(Bx)
             f()
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            f()
-            torch.cuda.synchronize()
-            t = time.perf_counter() - t0
+            t = float("inf")
+            for _ in range(3):
+                t0 = time.perf_counter()
+                f()
+                torch.cuda.synchronize()
+                t = min(t, time.perf_counter() - t0)
             if best is None or t < best[1]:
                 best = (Bx, t)
         return best[0]
