@@ -306,7 +306,7 @@ typedef struct nk_server_opts {
     double mem_budget_bytes; /* device bytes for per-request state; 0 = 60% of free */
     int32_t max_inflight;    /* requests on the GPU at once (streams); 0 = 8 */
     int32_t batch;           /* sources per launch for served requests (64/128/256);
-                                0 = by graph size: 256 up to 4M arcs, else 128 */
+                                0 = 128 (narrower when k is smaller) */
     double timeout_s;        /* bound on device-side waits; 0 = 10 s */
     int32_t no_pack;         /* 1: never pack small requests into one launch */
     int32_t reserved[7];
@@ -338,7 +338,7 @@ void nk_server_destroy(nk_server *srv);
  * must stay valid until nk_serve_poll returns something other than NK_PENDING.
  * Admission is by the device-memory budget; requests larger than the whole budget are
  * rejected with NK_ERR_NOMEM.  Consecutive small requests (graphs of up to 4M arcs,
- * k <= 128) are packed into one launch of up to 256 sources on the block-diagonal union
+ * k <= 256) are packed, up to 1024 sources, into launches of 128 sources on the block-diagonal union
  * of their graphs (BFS trees never cross graphs, so each request's scores are those of
  * the request alone, up to FP summation order). */
 int nk_serve_submit(nk_server *srv, const nk_graph *g, uint64_t seed, int32_t k,

@@ -77,13 +77,13 @@ struct nk_server {
 namespace nk {
 namespace {
 
-// Sources per launch for a request: on graphs of up to 4M arcs a launch costs about the
-// same whatever its width (the level count and its synchronisation dominate), so small
-// requests take 256 sources per launch (one or few launches); larger graphs take the
-// server's batch width.  Never wider than k rounded up to 64.
-int request_batch(const nk_server *S, const nk_graph *g, int32_t k)
+// Sources per launch for a request: the server's batch width if the caller fixed one, else
+// 128 (on the mixed serving load the 128-source sweep does more per second than the
+// 256-source one, whose wider gather rounds cost more than the extra launches save).  Never
+// wider than k rounded up to 64.
+int request_batch(const nk_server *S, const nk_graph *, int32_t k)
 {
-    int B = S->batch_fixed ? S->batch : (g->A <= (4ll << 20) ? 256 : 128);
+    int B = S->batch_fixed ? S->batch : 128;
     while (B > 64 && (B >> 1) >= k) B >>= 1;
     return B;
 }
@@ -139,13 +139,13 @@ int run_request(nk_server *S, Request *r, cudaStream_t st, double **h_buf, size_
 // ---------------------------------------------------------------- packed launches
 // A request is small when its graph has at most 4M arcs and k <= 256; small requests
 // waiting in the queue (the first kPackLookahead entries, larger requests keep their
-// order) share launches of 256 sources, up to 1024 sources per pack, on the
+// order) share launches of 128 sources, up to 1024 sources per pack, on the
 // block-diagonal union of their graphs: vertex ids of member r are shifted by the vertices of the members before it,
 // its sources by the same amount, so the BFS trees of different members never meet and
 // each member's slice of the union scores is its own result.
 constexpr int64_t kSmallArcs = 4ll << 20;
-constexpr int kPackWidth = 256;      // sources per launch of a pack
-constexpr int kPackSources = 1024;   // sources per pack (up to four launches)
+constexpr int kPackWidth = 128;      // sources per launch of a pack
+constexpr int kPackSources = 1024;   // sources per pack (up to eight launches)
 constexpr int kPackMembers = 32;
 constexpr int kPackLookahead = 64;   // queued requests a pack may pick from
 constexpr int64_t kPackVertices = 4ll << 20;
@@ -253,7 +253,7 @@ int run_pack(nk_server *S, const std::vector<Request *> &rs, cudaStream_t st, do
     }
     RunCfg cfg;
     cfg.mode = NK_MODE_BATCHED;
-    cfg.batch = k_u > 128 ? kPackWidth : (k_u > 64 ? 128 : 64);
+    cfg.batch = k_u > 64 ? kPackWidth : 64;
     cfg.ws = ws;
     cfg.grid_ctas = (int)std::min<int64_t>(std::max<int64_t>(A_u / 8192, 128), 1 << 20);
     cfg.grid_div = 2;
@@ -298,7 +298,7 @@ void worker(nk_server *S)
             S->queue.pop_front();
             need = job[0]->need;
             // pack the small requests that follow, in arrival order, while they fit
-            // (a pack runs 256 sources wide: its members' bytes are counted at that width)
+            // (a pack runs kPackWidth sources wide: its members' bytes are counted at that width)
             if (S->pack && small_request(job[0])) {
                 int64_t k = job[0]->k, nv = job[0]->g->n;
                 size_t pneed = request_bytes(job[0]->g, kPackWidth, job[0]->k);
