@@ -97,19 +97,6 @@ __device__ __forceinline__ void src_mark(const SrcArgs &a, int &ti, int level, i
     }
 }
 
-template <int TPV> struct Lanes {
-    int lane, lg, gw;
-    long long wid, nw;
-    __device__ Lanes()
-    {
-        lane = threadIdx.x & 31;
-        lg = lane % TPV;
-        gw = lane / TPV;
-        wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-        nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    }
-};
-
 __device__ __forceinline__ int degree(const int32_t *rp, int v) { return __ldg(rp + v + 1) - __ldg(rp + v); }
 
 // A row is processed in chunks only when a chunk table exists (a.H > 0, which holds
