@@ -200,6 +200,16 @@ def committed_traffic(config, batch, relabel=False):
 
 
 NOMINAL_HBM_GBS = 7900.0  # HBM3e nominal bandwidth of one GB300
+L2_BYTES = 129 * 1024 * 1024  # GB300 L2
+
+
+def l2_note(n, A, B):
+    """How the timed steps stand to L2: flushed between steps, and whether one launch's
+    working set (the CSR and the sweep state of B sources, 12 bytes per vertex and source)
+    is larger than L2."""
+    ws = 4 * (n + 1) + 4 * A + 12 * n * B
+    size = "larger than L2" if ws > L2_BYTES else "within L2"
+    return f"flushed (256 MiB write) between steps; one launch's working set ({ws / 2**20:.0f} MiB) {size}"
 
 
 def measured_peaks():
@@ -631,7 +641,8 @@ def run_ours(args, world, rank, local):
     k = cfg["k"]
 
     if exact:
-        opts = nk.run_opts(mode=nk.MODE_BATCHED, batch=args.batch or 64)
+        # all n sources; the autotuner times its trial launches on the graph's own sources
+        opts = nk.autotune(g, sseed, k) if not args.batch else nk.run_opts(mode=nk.MODE_BATCHED, batch=args.batch)
         src_dev = torch.arange(n, dtype=torch.int32, device="cuda")
     else:
         opts = nk.autotune(g, sseed, k) if not args.batch else nk.run_opts(
@@ -727,7 +738,7 @@ def run_ours(args, world, rank, local):
                       "relabelled": relabelled,
                       "max_depth": stats["max_depth"],
                       "td_levels": stats["td_levels"], "bu_levels": stats["bu_levels"],
-                      "l2": "flushed (256 MiB write) between steps; working set far larger than L2",
+                      "l2": l2_note(n, A, B),
                       "sigma": "uint64",
                       "parallelism": (f"one sampled set split over {world} GPUs, one NCCL all-reduce of n doubles"
                                       if world > 1 else "1 GPU")},
