@@ -141,7 +141,10 @@ int nk_sssp_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col, int64
 
 /* ---------------------------------------------------------------- betweenness */
 #define NK_MODE_AUTO 0       /* batched where it fits, per-source otherwise */
-#define NK_MODE_PER_SOURCE 1 /* plain per-source kernel (one BFS tree at a time) */
+#define NK_MODE_PER_SOURCE 1 /* plain per-source kernel (one BFS tree at a time); backward levels
+                                whose successors carry few arcs add psi with FP64 atomics, so the
+                                last bits of its scores may differ from run to run (distances and
+                                path counts never do) */
 #define NK_MODE_BATCHED 2    /* bitset multi-source kernel, `batch` sources per launch */
 
 #define NK_DIR_AUTO 0        /* direction-optimising: switch by alpha */
